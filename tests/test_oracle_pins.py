@@ -1,0 +1,338 @@
+"""Pins of the CPU oracle against what the paper and the mathematics fix.
+
+None of these compares the oracle with itself: each checks it against dense
+matrices, closed forms, invariants, exact free-fermion energies, or numbers
+printed in the paper.
+"""
+import itertools
+import json
+import math
+import os
+
+import numpy as np
+import pytest
+
+import oracle
+import workloads as wl
+from oracle import dense
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def _coeff_dict(o):
+    x, z, c = o.terms()
+    return {(int(x[i, 0]), int(z[i, 0])): c[i] for i in range(len(c))}
+
+
+# ---------------------------------------------------------------------------
+# Bit algebra: commutation and the phase of Q*P against dense matrices.
+# ---------------------------------------------------------------------------
+@pytest.mark.parametrize("n", [1, 2, 3])
+def test_product_and_commutation_vs_dense(n):
+    xs, zs = dense.all_strings(n)
+    mats = [dense.pauli_dense(xs[i], zs[i], n) for i in range(xs.shape[0])]
+    index = {(int(xs[i, 0]), int(zs[i, 0])): i for i in range(xs.shape[0])}
+    phase = [1, 1j, -1, -1j]
+    for q in range(xs.shape[0]):
+        for p in range(xs.shape[0]):
+            Q, P = mats[q], mats[p]
+            comm = np.allclose(Q @ P, P @ Q)
+            assert oracle.commutes(1, xs[p], zs[p], xs[q], zs[q]) == comm
+            e, rx, rz = oracle.pauli_product(1, xs[q], zs[q], xs[p], zs[p])
+            R = mats[index[(int(rx[0]), int(rz[0]))]]
+            assert np.allclose(Q @ P, phase[e] * R)
+
+
+# single-site multiplication table of the Pauli group (textbook):
+# a*b = phase * c for letters in {I, X, Y, Z}
+_TABLE = {
+    ("I", "I"): (1, "I"), ("I", "X"): (1, "X"), ("I", "Y"): (1, "Y"), ("I", "Z"): (1, "Z"),
+    ("X", "I"): (1, "X"), ("X", "X"): (1, "I"), ("X", "Y"): (1j, "Z"), ("X", "Z"): (-1j, "Y"),
+    ("Y", "I"): (1, "Y"), ("Y", "X"): (-1j, "Z"), ("Y", "Y"): (1, "I"), ("Y", "Z"): (1j, "X"),
+    ("Z", "I"): (1, "Z"), ("Z", "X"): (1j, "Y"), ("Z", "Y"): (-1j, "X"), ("Z", "Z"): (1, "I"),
+}
+_LET = {(0, 0): "I", (1, 0): "X", (0, 1): "Z", (1, 1): "Y"}
+_BITS = {v: k for k, v in _LET.items()}
+
+
+def _letters(x, z, n):
+    return [_LET[((int(x[i // 64]) >> (i % 64)) & 1, (int(z[i // 64]) >> (i % 64)) & 1)]
+            for i in range(n)]
+
+
+@pytest.mark.parametrize("n", [64, 65, 100, 128])
+def test_product_multiword_vs_letter_table(n):
+    rng = np.random.default_rng(n)
+    W = wl.n_words(n)
+    for _ in range(200):
+        qx = np.zeros(W, np.uint64); qz = np.zeros(W, np.uint64)
+        px = np.zeros(W, np.uint64); pz = np.zeros(W, np.uint64)
+        for i in range(n):
+            for arr_x, arr_z in ((qx, qz), (px, pz)):
+                a, b = _BITS["IXYZ"[rng.integers(0, 4)]]
+                if a:
+                    arr_x[i // 64] |= np.uint64(1) << np.uint64(i % 64)
+                if b:
+                    arr_z[i // 64] |= np.uint64(1) << np.uint64(i % 64)
+        ph = 1
+        out = []
+        for a, b in zip(_letters(qx, qz, n), _letters(px, pz, n)):
+            f, c = _TABLE[(a, b)]
+            ph *= f
+            out.append(c)
+        e, rx, rz = oracle.pauli_product(W, qx, qz, px, pz)
+        assert _letters(rx, rz, n) == out
+        assert [1, 1j, -1, -1j][e] == ph
+        anti = sum(1 for a, b in zip(_letters(qx, qz, n), _letters(px, pz, n))
+                   if a != "I" and b != "I" and a != b) % 2
+        assert oracle.commutes(W, px, pz, qx, qz) == (anti == 0)
+
+
+# ---------------------------------------------------------------------------
+# delta = 0: the propagated operator equals the dense Trotter product
+# (Sec. III.A: without truncation ITPP reproduces Trotterized evolution).
+# ---------------------------------------------------------------------------
+def _compare_dense(H, dtau, n_layers, tol=1e-12):
+    o = oracle.Oracle(H.n, H.gate_x, H.gate_z, H.alpha, dtau, 0.0)
+    o.apply_layers(n_layers)
+    got = _coeff_dict(o)
+    rho = dense.trotter_rho(H, dtau, n_layers)
+    ref = dense.pauli_coefficients(rho, H.n)
+    scale = max(abs(v) for v in ref.values())
+    for k, v in ref.items():
+        assert abs(v.imag) < 1e-12 * scale           # Hermitian: real coefficients
+        assert abs(got.get(k, 0.0) - v.real) <= tol * scale, (k, got.get(k), v)
+    assert got[(0, 0)] == 1.0
+    return o
+
+
+@pytest.mark.parametrize("seed", [1, 2, 3])
+def test_delta0_random_hamiltonian_vs_dense(seed):
+    H = wl.random_pauli_hamiltonian(3, 7, seed)
+    _compare_dense(H, 0.21, 3)
+
+
+def test_delta0_random_hamiltonian_n4_vs_dense():
+    H = wl.random_pauli_hamiltonian(4, 9, 11, max_weight=3)
+    _compare_dense(H, 0.13, 2)
+
+
+@pytest.mark.parametrize("periodic", [False, True])
+def test_delta0_tfim_vs_dense(periodic):
+    H = wl.tfim_1d(4, 1.0, 0.7, periodic=periodic)
+    _compare_dense(H, 0.1, 6)
+
+
+def test_single_gate_on_random_operator_vs_dense():
+    # one gate of every letter pattern acting on a random Hermitian operator
+    n = 3
+    rng = np.random.default_rng(7)
+    xs, zs = dense.all_strings(n)
+    c = rng.normal(size=xs.shape[0])
+    c[0] = 1.0   # identity (x = z = 0) first in all_strings
+    assert xs[0, 0] == 0 and zs[0, 0] == 0
+    rho0 = sum(c[i] * dense.pauli_dense(xs[i], zs[i], n) for i in range(xs.shape[0]))
+    H = wl.random_pauli_hamiltonian(n, 12, 3)
+    for k in range(H.n_gates):
+        o = oracle.Oracle(n, H.gate_x, H.gate_z, H.alpha, 0.37, 0.0)
+        o.set_terms(xs, zs, c)
+        o.apply_gate(k)
+        got = _coeff_dict(o)
+        rho = dense.trotter_rho(H, 0.37, 1, rho0=rho0, gates=[k])
+        ref = dense.pauli_coefficients(rho, n)
+        for key, v in ref.items():
+            assert abs(got.get(key, 0.0) - v.real) < 1e-12
+
+
+# ---------------------------------------------------------------------------
+# Closed forms
+# ---------------------------------------------------------------------------
+def test_first_gate_on_identity():
+    # I -> cosh(theta) I - sinh(theta) Q, normalised: {I: 1, Q: -tanh(theta)}
+    H = wl.random_pauli_hamiltonian(5, 1, 4)
+    o = oracle.Oracle(5, H.gate_x, H.gate_z, H.alpha, 0.3, 0.0)
+    o.apply_gate(0)
+    x, z, c = o.terms()
+    theta = H.alpha[0] * 0.3
+    d = {(int(x[i, 0]), int(z[i, 0])): c[i] for i in range(len(c))}
+    assert d == {(0, 0): 1.0,
+                 (int(H.gate_x[0, 0]), int(H.gate_z[0, 0])): d[(int(H.gate_x[0, 0]),
+                                                                  int(H.gate_z[0, 0]))]}
+    assert abs(d[(int(H.gate_x[0, 0]), int(H.gate_z[0, 0]))] + math.tanh(theta)) < 1e-15
+
+
+def test_single_spin_sign_convention():
+    # H = -h X: <X>_beta = tanh(beta h) > 0 (alpha = -h, theta = alpha dtau)
+    for h, dtau, L in ((1.0, 0.05, 20), (0.3, 0.1, 7)):
+        H = wl.tfim_1d(1, 1.0, h)
+        o = oracle.Oracle(1, H.gate_x, H.gate_z, H.alpha, dtau, 0.0)
+        o.apply_layers(L)
+        X = wl.x_observables(1)[0]
+        assert abs(o.expect(X) - math.tanh(h * L * dtau)) < 1e-14
+
+
+@pytest.mark.parametrize("periodic", [False, True])
+def test_commuting_hamiltonian_zz_closed_form(periodic):
+    # h = 0: all terms commute, C = 0, Trotter is exact (App. B)
+    n, J, dtau, L = 5, 0.8, 0.1, 9
+    H = wl.tfim_1d(n, J, 0.0, periodic=periodic)
+    o = oracle.Oracle(n, H.gate_x, H.gate_z, H.alpha, dtau, 0.0)
+    o.apply_layers(L)
+    t = math.tanh(J * L * dtau)
+    x, z = wl.two_site(n, 1, 2, "Z", "Z")
+    got = o.coeffs(x[None], z[None])[0]
+    want = (t + t ** (n - 1)) / (1 + t ** n) if periodic else t
+    assert abs(got - want) < 1e-13
+    E = o.expect(wl.energy_observable(H))
+    n_b = n if periodic else n - 1
+    assert abs(E - (-n_b * J * want)) < 1e-12
+
+
+def test_product_state_x_strings():
+    # J = 0: the coefficient of X_S is tanh(beta h)^|S|
+    n, h, dtau, L = 4, 0.9, 0.07, 5
+    H = wl.tfim_1d(n, 0.0, h)
+    o = oracle.Oracle(n, H.gate_x, H.gate_z, H.alpha, dtau, 0.0)
+    o.apply_layers(L)
+    d = _coeff_dict(o)
+    t = math.tanh(h * L * dtau)
+    assert len(d) == 2 ** n
+    for S in range(2 ** n):
+        assert abs(d[(S, 0)] - t ** bin(S).count("1")) < 1e-14
+
+
+# ---------------------------------------------------------------------------
+# Truncation reading: keep |c| > delta on the merged, un-normalised values,
+# then divide by the identity coefficient.
+# ---------------------------------------------------------------------------
+def test_threshold_strict_and_before_normalisation():
+    n = 2
+    H = wl.tfim_1d(n, 1.0, 1.0)                  # gates: Z0Z1, X0, X1
+    a = 0.125                                    # exactly representable
+    xA, zA = wl.two_site(n, 0, 1, "X", "I")       # X0 anticommutes with Z0Z1
+    xs = np.stack([np.zeros(1, np.uint64), xA]); zs = np.stack([np.zeros(1, np.uint64), zA])
+    for delta, present in ((a, False), (np.nextafter(a, 0.0), True)):
+        o = oracle.Oracle(n, H.gate_x, H.gate_z, H.alpha, 0.1, delta)
+        o.set_terms(xs, zs, np.array([1.0, a]))
+        o.apply_gate(0)                          # X0 passes through with c = a exactly
+        d = _coeff_dict(o)
+        key = (int(xA[0]), int(zA[0]))
+        assert (key in d) == present
+        if present:
+            assert d[key] == a / math.cosh(-1.0 * 0.1)   # normalised afterwards
+
+
+def test_cap_keeps_largest_with_key_tiebreak():
+    n = 6
+    H = wl.tfim_1d(n, 1.0, 1.0)
+    rng = np.random.default_rng(3)
+    X, Z, C = wl.synthetic_state(n, 300, 5, delta=1e-3)
+    C[1:] = np.round(C[1:] * 8) / 8               # many exact ties
+    C[1:][C[1:] == 0] = 0.125
+    M = 120
+    o = oracle.Oracle(n, H.gate_x, H.gate_z, H.alpha, 0.05, 0.0, cap_M=M, cap_policy=1)
+    o.set_terms(X, Z, C)
+    ref = oracle.Oracle(n, H.gate_x, H.gate_z, H.alpha, 0.05, 0.0)
+    ref.set_terms(X, Z, C)
+    k = n  # first X gate
+    o.apply_gate(k)
+    ref.apply_gate(k)
+    assert ref.count() > M
+    kept = _coeff_dict(o)
+    full = _coeff_dict(ref)
+    assert len(kept) == M
+    assert set(kept) <= set(full)
+    # the same normaliser (identity kept) -> values agree
+    for key, v in kept.items():
+        assert v == full[key]
+    kmin = min(abs(v) for v in kept.values())
+    dropped = [(key, abs(v)) for key, v in full.items() if key not in kept]
+    assert all(dv <= kmin for _, dv in dropped)
+    tie_kept = [key for key, v in kept.items() if abs(v) == kmin]
+    tie_drop = [key for key, dv in dropped if dv == kmin]
+    if tie_drop:
+        assert max(tie_kept) < min(tie_drop)
+
+
+# ---------------------------------------------------------------------------
+# Invariants of the TFIM propagation
+# ---------------------------------------------------------------------------
+def _popc(v):
+    return bin(int(v)).count("1")
+
+
+@pytest.mark.parametrize("n,periodic", [(2, False), (3, False), (4, False), (5, False),
+                                        (6, False), (3, True), (4, True), (5, True)])
+def test_saturated_support_is_central_binomial(n, periodic):
+    H = wl.tfim_1d(n, 1.0, 0.5, periodic=periodic)
+    o = oracle.Oracle(n, H.gate_x, H.gate_z, H.alpha, 0.04, 0.0)
+    prev = -1
+    for _ in range(60):
+        o.apply_layers(1)
+        c = o.count()
+        assert c <= math.comb(2 * n, n)
+        if c == prev:
+            break
+        prev = c
+    assert o.count() == math.comb(2 * n, n)
+    x, z, cc = o.terms()
+    for i in range(len(cc)):
+        assert _popc(z[i, 0]) % 2 == 0          # spin-flip symmetric
+        assert _popc(x[i, 0] & z[i, 0]) % 2 == 0  # real density matrix
+        assert int(x[i, 0]) >> n == 0 and int(z[i, 0]) >> n == 0
+    assert _coeff_dict(o)[(0, 0)] == 1.0
+
+
+def test_paper_untruncated_count_is_central_binomial():
+    g = json.load(open(os.path.join(GOLDEN, "paper_numbers.json")))
+    assert math.comb(24, 12) == g["untruncated_support_N12"]["value"]
+
+
+# ---------------------------------------------------------------------------
+# Physics: exact diagonalisation, free fermions, first-order convergence.
+# ---------------------------------------------------------------------------
+@pytest.mark.parametrize("n,h", [(5, 0.7), (6, 1.0), (7, 1.3)])
+def test_bdg_energy_vs_exact_diagonalisation(n, h):
+    H = wl.tfim_1d(n, 1.0, h)
+    E = wl.energy_observable(H)
+    for beta in (0.2, 1.0, 2.5):
+        assert abs(dense.thermal_expect(H, beta, E) - dense.bdg_energy(1.0, [h] * n, beta)) < 1e-10
+
+
+def test_trotter_error_first_order_vs_ed():
+    n, beta = 6, 1.0
+    H = wl.tfim_1d(n, 1.0, 1.0)
+    E = wl.energy_observable(H)
+    exact = dense.bdg_energy(1.0, [1.0] * n, beta)
+    errs = []
+    for dtau in (0.1, 0.05, 0.025):
+        o = oracle.Oracle(n, H.gate_x, H.gate_z, H.alpha, dtau, 0.0)
+        o.apply_layers(int(round(beta / dtau)))
+        errs.append(abs(o.expect(E) - exact))
+    # The bound of Sec. II.C / App. C is first order in dtau.  rho = S^dag S
+    # is a palindromic product, so the observed error of <H> falls faster
+    # (ratio ~4 per halving); the pin is "at least first order".
+    r1, r2 = errs[0] / errs[1], errs[1] / errs[2]
+    assert r1 > 1.8 and r2 > 1.8, errs
+    assert errs[2] < 2e-4
+
+
+def test_energy_matches_dense_trotter_trace():
+    n, dtau, L = 5, 0.1, 5
+    H = wl.tfim_1d(n, 1.0, 0.8)
+    o = oracle.Oracle(n, H.gate_x, H.gate_z, H.alpha, dtau, 0.0)
+    o.apply_layers(L)
+    rho = dense.trotter_rho(H, dtau, L)
+    ref = np.real(np.trace(dense.hamiltonian_dense(H) @ rho) / np.trace(rho))
+    assert abs(o.expect(wl.energy_observable(H)) - ref) < 1e-12
+
+
+def test_high_temperature_series():
+    # <H> = -beta Tr(H^2)/2^n + O(beta^3) on a bipartite lattice
+    L = 3
+    H = wl.tfim_2d(L, 1.0, 0.7)
+    o = oracle.Oracle(H.n, H.gate_x, H.gate_z, H.alpha, 0.002, 0.0)
+    o.apply_layers(5)
+    beta = 0.01
+    series = -beta * float(np.sum(H.alpha ** 2))
+    assert abs(o.expect(wl.energy_observable(H)) - series) < 5e-3 * abs(series)
