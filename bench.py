@@ -1,0 +1,381 @@
+"""Benchmark: Pauli terms per second per Trotter gate on one GB300 (or N replicas).
+
+Workload (default): the 1D transverse-field Ising chain with n = 64 periodic
+sites at the critical point J = h = 1, dtau = 0.01, coefficients |c| <= 1e-6
+dropped and at most 2^26 terms kept (top-M), FP64 coefficients, 1 uint64 word
+per mask.  The state grows from the identity and reaches the 2^26 bound after
+eleven Trotter layers; the set-up phase runs those layers untimed, and every
+benchmark step is one further Trotter layer (128 elementary gates) applied to
+the state resident in HBM.  The state (2^26 terms, 1.6 GB, plus the 3.2 GB of
+children per gate) is far larger than the 126 MB L2, so no flush is needed.
+
+Metric: sum over the timed gates of the input term count N_in, divided by the
+device time of the timed steps (CUDA events on the library's stream, max over
+ranks).  With --gpus N > 1 every rank runs an independent replica (the
+workload has no data-path exchange); value is the total over ranks.
+
+--impl reference runs the CPU oracle (the plain restatement of Algorithm 1)
+on the host cores, on a bounded prefix of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+import workloads as wl  # noqa: E402
+
+METRIC = "Pauli terms/s per Trotter gate"
+UNIT = "terms/s"
+KERNEL_NAMES = {0: "k_gate_insert (merge-table build)",
+                1: "k_gate_main (branch-emit-merge-truncate)",
+                2: "top-M select chain (k_cap_*, k_tie_*)",
+                3: "expectation (k_obs_*)"}
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--workload", default="tfim1d_n64_periodic")
+    ap.add_argument("--cap-log2", type=int, default=0,
+                    help="override the term bound (2^k); 0 keeps the workload's")
+    ap.add_argument("--setup-layers", type=int, default=-1,
+                    help="untimed layers before warm-up (-1: until the bound is reached)")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--ref-gates", type=int, default=160,
+                    help="oracle gates per reference step (bounded CPU sample)")
+    return ap.parse_args()
+
+
+def load_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        d = json.load(open(p))
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled during the timed region."""
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax.append(float(f[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": float(max(smax)),
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def dist_init():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch.distributed as dist
+        backend = "nccl"
+        dist.init_process_group(backend=backend)
+    return world, rank, local
+
+
+def barrier(world):
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+        dist.barrier(device_ids=[torch.cuda.current_device()])
+
+
+def max_over_ranks(world, v):
+    if world == 1:
+        return v
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([v], dtype=torch.float64, device="cuda")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def sum_over_ranks(world, v):
+    if world == 1:
+        return v
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([v], dtype=torch.float64, device="cuda")
+    dist.all_reduce(t, op=dist.ReduceOp.SUM)
+    return float(t.item())
+
+
+# ---------------------------------------------------------------------------
+# CPU oracle timing (the reported baseline and the reference arm)
+# ---------------------------------------------------------------------------
+def oracle_sample(w, n_gates_budget):
+    """Run the oracle from the identity over the first gates of the workload;
+    returns (terms processed, seconds, gates)."""
+    import oracle
+    o = oracle.Oracle.from_workload(w)
+    terms, gates, t0 = 0, 0, time.perf_counter()
+    k = 0
+    while gates < n_gates_budget:
+        terms += o.count()
+        o.apply_gate(k)
+        k = (k + 1) % w.H.n_gates
+        gates += 1
+    dt = time.perf_counter() - t0
+    o.close()
+    return terms, dt, gates
+
+
+def run_reference(args, w):
+    world, rank, _ = int(os.environ.get("WORLD_SIZE", "1")), int(os.environ.get("RANK", "0")), 0
+    if rank != 0:
+        return 0
+    cores = 1   # the oracle is single-threaded
+    for _ in range(args.warmup):
+        oracle_sample(w, max(1, args.ref_gates // 4))
+    tot_terms, tot_t = 0, 0.0
+    for _ in range(args.steps):
+        t, dt, g = oracle_sample(w, args.ref_gates)
+        tot_terms += t
+        tot_t += dt
+    v = tot_terms / tot_t
+    sample = (f"{w.name}: the first {args.ref_gates} gates from the identity "
+              f"(Trotter order, single thread), {args.steps} steps")
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 1e3 * tot_t / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": w.name},
+            "cpu_baseline": {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle",
+                             "sample": sample},
+            "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# ---------------------------------------------------------------------------
+# GPU arm
+# ---------------------------------------------------------------------------
+def main():
+    args = parse()
+    w = wl.WORKLOADS[args.workload]
+    if args.cap_log2:
+        w.cap_M = 1 << args.cap_log2
+    if args.impl == "reference":
+        return run_reference(args, w)
+
+    import torch
+    world, rank, local = dist_init()
+    torch.cuda.set_device(local)
+    import paper_2601_14400_gb300 as itpp
+    if not os.path.exists(itpp.LIB_PATH):
+        itpp.build()
+
+    stream = torch.cuda.Stream()
+    g = itpp.Propagator.from_workload(w, stream=stream)
+    W = w.H.W
+    term_bytes = 16 * W + 8
+
+    # set-up: grow the state to the bound (untimed)
+    setup = 0
+    limit = args.setup_layers if args.setup_layers >= 0 else 40
+    while setup < limit:
+        g.apply_trotter_layer(1)
+        setup += 1
+        if args.setup_layers < 0 and g.count() >= w.cap_M:
+            break
+    for _ in range(args.warmup):
+        g.apply_trotter_layer(1)
+    g.synchronize()
+
+    # timed region
+    st0 = g.stats()
+    g.profile_enable(True)
+    clocks = ClockSampler(local)
+    clocks.start()
+    barrier(world)
+    torch.cuda.synchronize()
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    g.apply_trotter_layer(args.steps)
+    ev1.record(stream)
+    g.synchronize()
+    torch.cuda.synchronize()
+    barrier(world)
+    clk = clocks.stop()
+    ms = ev0.elapsed_time(ev1)
+    st1 = g.stats()
+    prof = {k: g.profile_read(k) for k in range(4)}
+    g.profile_enable(False)
+
+    terms_in = st1["terms_in"] - st0["terms_in"]
+    terms_out = st1["terms_out"] - st0["terms_out"]
+    gates = st1["gates_applied"] - st0["gates_applied"]
+    launches = st1["kernel_launches"] - st0["kernel_launches"]
+    ms_max = max_over_ranks(world, ms)
+    total_terms = sum_over_ranks(world, float(terms_in))
+    value = total_terms / (ms_max * 1e-3)
+
+    # roofline of the dominant kernel class and of the whole gate
+    peak, peak_kind = load_peaks()
+    dom = max(prof, key=lambda k: prof[k][1])
+    n_dom, ms_dom = prof[dom]
+    # algorithmic bytes of one elementary gate: every input term read once,
+    # every kept term written once
+    b_alg_gate = (terms_in + terms_out) * term_bytes / max(gates, 1)
+    if dom == 0:
+        # the table build reads each input key once (coefficients of the
+        # commuting terms are not counted)
+        b_alg_dom = terms_in * (16 * W) / max(gates, 1)
+    elif dom == 1:
+        b_alg_dom = b_alg_gate
+    else:
+        b_alg_dom = (terms_out) * 8 / max(gates, 1)
+    achieved_dom = b_alg_dom / (ms_dom / max(n_dom, 1) * 1e-3) / 1e9
+    gate_ms = sum(prof[k][1] for k in (0, 1, 2)) / max(gates, 1)
+    achieved_gate = b_alg_gate / (gate_ms * 1e-3) / 1e9
+    traffic = None
+    tr_path = os.path.join(ROOT, "profiles", "traffic.json")
+    if os.path.exists(tr_path):
+        tr = json.load(open(tr_path))
+        if tr.get("kernel_class") == dom and tr.get("source_digest") == source_digest():
+            traffic = tr.get("bytes_per_launch")
+
+    # end to end through the public API with host buffers: one layer, then
+    # the energy and <Z0 Z1> read to host (observable strings copied in)
+    e2e = None
+    if not args.no_e2e:
+        E = w.observables["energy"]
+        Z = w.observables.get("Z0Z1")
+        obs = [o for o in (E, Z) if o is not None]
+        h2d = sum(o.x.nbytes + o.z.nbytes + o.w.nbytes for o in obs)
+        d2h = 8 * len(obs)
+        sc = g.stats()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        vals = []
+        for _ in range(args.steps):
+            g.apply_trotter_layer(1)
+            vals.append([g.expect(o) for o in obs])
+        t1 = time.perf_counter()
+        se = g.stats()
+        e_terms = sum_over_ranks(world, float(se["terms_in"] - sc["terms_in"]))
+        e_ms = max_over_ranks(world, (t1 - t0) * 1e3)
+        e2e = {"value": e_terms / (e_ms * 1e-3), "unit": UNIT,
+               "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h),
+               "last_observables": {"energy": vals[-1][0],
+                                    "Z0Z1": vals[-1][1] if len(vals[-1]) > 1 else None}}
+
+    cpu = None
+    if rank == 0 and not args.no_cpu_baseline:
+        t, dt, ng = oracle_sample(w, args.ref_gates)
+        cpu = {"value": t / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
+               "sample": f"{w.name}: first {ng} gates from the identity, single thread "
+                         f"({t} term-gates in {dt:.1f} s)"}
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_max / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic",
+            "config": {"workload": w.name, "n": w.H.n, "mask_words": W,
+                       "dtau": w.dtau, "delta": w.delta, "cap_M": w.cap_M,
+                       "cap_policy": "top-M" if w.cap_policy else "error",
+                       "gates_per_step": w.H.n_gates, "setup_layers": setup,
+                       "terms_at_start": st0["count"],
+                       "l2": "state larger than L2 (no flush)",
+                       "parallelism": f"replicas x{world}"},
+            "roofline": {"bound": "hbm", "kernel": KERNEL_NAMES[dom],
+                         "achieved": achieved_dom, "peak": peak, "unit": "GB/s",
+                         "frac": achieved_dom / peak, "traffic": traffic,
+                         "peak_source": peak_kind,
+                         "alg_bytes_per_launch": b_alg_dom,
+                         "avg_launch_ms": ms_dom / max(n_dom, 1)},
+            "gate_roofline": {"achieved": achieved_gate, "peak": peak, "unit": "GB/s",
+                              "frac": achieved_gate / peak, "alg_bytes_per_gate": b_alg_gate,
+                              "gate_ms": gate_ms},
+            "kernel_time_share": {KERNEL_NAMES[k]: prof[k][1] / max(1e-9, sum(
+                prof[j][1] for j in prof)) for k in prof},
+            "clocks": clk,
+            "e2e": e2e,
+            "cpu_baseline": cpu,
+            "gpu_launches": int(launches),
+            "timed_gates": int(gates),
+            "terms_in_timed": int(terms_in),
+        }
+        print(json.dumps(line), flush=True)
+    g.close()
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+    return 0
+
+
+def source_digest():
+    import hashlib
+    h = hashlib.sha256()
+    d = os.path.join(ROOT, "paper_2601_14400_gb300", "csrc")
+    for f in sorted(os.listdir(d)):
+        h.update(open(os.path.join(d, f), "rb").read())
+    return h.hexdigest()[:16]
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,224 @@
+/*
+ * itpp.h -- C ABI of the GB300 imaginary-time Pauli propagation library.
+ *
+ * The library propagates the identity operator through a first-order Trotter
+ * product of imaginary-time Pauli gates (Algorithm 1 of "Pauli Propagation
+ * for Imaginary-Time Evolution", arXiv 2601.14400) and reads thermal
+ * expectation values from the propagated operator.  Every step of the
+ * method runs in hand-written sm_103a CUDA kernels; the host side only
+ * validates arguments, computes the per-gate weights once and orders the
+ * launches.
+ *
+ * Representation (Eq. (Observable_Pauli), Sec. II.B):
+ *   A Pauli string on n sites is a pair of masks (x, z) of W = ceil(n/64)
+ *   uint64 words; site i is bit i%64 of word i/64.  (x_i, z_i) = (0,0) I,
+ *   (1,0) X, (0,1) Z, (1,1) Y (the Hermitian Y, not XZ).  Bits >= n must be
+ *   zero.  Host arrays of strings are row-major: string j occupies words
+ *   [j*W, (j+1)*W) of the x array and of the z array.  1 <= n <= 128.
+ *
+ * Conventions shared by every call:
+ *   - Every call returns itpp_status.  Calls that launch work are
+ *     asynchronous on the handle's CUDA stream; an error detected on the
+ *     device (capacity, hash probe limit, trace collapse) is stored in the
+ *     handle and returned by the next synchronising call (itpp_synchronize,
+ *     itpp_get_count, itpp_get_terms, itpp_expect, itpp_coeffs).  Once a
+ *     handle holds an error every later call returns it; destroy still works.
+ *   - The library owns all device memory it allocates for a handle and frees
+ *     it in itpp_destroy.  Caller pointers are only read or written during
+ *     the call (host arrays) or until the stream reaches the work (device
+ *     arrays of the *_device calls).
+ *   - A handle is not thread-safe; use one handle per host thread.
+ */
+#ifndef ITPP_H
+#define ITPP_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct itpp_ctx* itpp_handle;
+typedef struct itpp_batch_ctx* itpp_batch_handle;
+
+typedef enum {
+    ITPP_OK = 0,
+    ITPP_ERR_ARG = 1,         /* invalid argument (checked on the host)            */
+    ITPP_ERR_ALLOC = 2,       /* a device or host allocation failed                */
+    ITPP_ERR_CAPACITY = 3,    /* more terms than cap_M with cap_policy 0, or a
+                                 buffer would overflow                              */
+    ITPP_ERR_HASH_PROBE = 4,  /* the merge table's probe limit was reached          */
+    ITPP_ERR_TIMEOUT = 5,     /* a device-side wait gave up (bounded spin)          */
+    ITPP_ERR_TRACE_ZERO = 6,  /* the identity coefficient was truncated or is
+                                 missing, so the trace cannot be normalised         */
+    ITPP_ERR_CUDA = 7,        /* a CUDA runtime call failed                         */
+    ITPP_ERR_STATE = 8        /* call not valid in the handle's current state       */
+} itpp_status;
+
+/* Propagation parameters.  Zero-initialise and set what you need. */
+typedef struct {
+    /* Coefficient threshold: after each gate keep a term iff |c| > delta
+     * (Sec. II.B "Coefficient threshold"; Algorithm 1, "Truncate").  The test
+     * is applied to the merged coefficients before the trace normalisation.
+     * Must be >= 0; 0 keeps every nonzero coefficient. */
+    double delta;
+    /* Term bound (Sec. II.C, "Practical considerations"): the most terms the
+     * state may hold after a gate.  Sizes the device buffers
+     * (2 * cap_M terms each, two of them) and the merge table. >= 1. */
+    uint64_t cap_M;
+    /* 0: a gate that leaves more than cap_M terms is an ITPP_ERR_CAPACITY
+     *    error ("terminating").
+     * 1: keep the cap_M largest |c| (ties: ascending key, words x[0..W-1]
+     *    then z[0..W-1] compared as unsigned), the K-truncation of Sec. II.C
+     *    applied only when the bound is exceeded ("adapting"). */
+    int cap_policy;
+    /* 0: open-addressing hash merge of the two children of each key (main);
+     * 1: sort-based merge -- all children are sorted by key and equal keys
+     *    reduced.  Both give bit-identical states. */
+    int merge_path;
+    /* Tuning (0 = library default or the autotuned value):
+     * table_load_pct: highest load of the merge table, in percent (10..75).
+     * block_threads: threads per CTA of the gate kernels (64..1024, /32).
+     * items_per_thread: terms per thread per tile (1..8). */
+    int table_load_pct;
+    int block_threads;
+    int items_per_thread;
+    int reserved[5];
+} itpp_params;
+
+/* Counters kept on the device and read by itpp_get_stats (synchronising). */
+typedef struct {
+    uint64_t gates_applied;   /* elementary gates since create / last load      */
+    uint64_t terms_in;        /* sum over gates of the input term count N_in    */
+    uint64_t terms_out;       /* sum over gates of the kept term count          */
+    uint64_t peak_terms;      /* largest kept term count after any gate         */
+    uint64_t cap_events;      /* gates where the cap_M bound fired              */
+    uint64_t count;           /* current term count                             */
+    uint64_t table_probes;    /* merge-table slots visited (build + lookups)    */
+    uint64_t kernel_launches; /* kernels this handle has launched (host count)  */
+} itpp_stats;
+
+/* ---------------------------------------------------------------------------
+ * Lifetime
+ * ------------------------------------------------------------------------- */
+
+/* Create a propagation of the Hamiltonian H = sum_k alpha_k Q_k
+ * (Algorithm 1, "Input"), with gates applied in the given order inside every
+ * Trotter layer.  The gate of term k is V_k = exp(-(dtau/2) alpha_k Q_k)
+ * (Sec. II.C, first-order Trotter product), whose propagation rule
+ * (Eq. (ITPP_PropRules)) uses the angle theta_k = alpha_k * dtau; the host
+ * computes cosh(theta_k) and sinh(theta_k) once here.  The state starts as
+ * the identity operator (Algorithm 1, "Initialize rho = I"; Sec. II.C: the
+ * 1/2^n of the maximally mixed state cancels).
+ *   n           number of sites, 1..128.
+ *   gate_x/z    host, n_gates * W words each, row-major; bits >= n zero.
+ *   alpha       host, n_gates real coefficients.
+ *   dtau        Trotter step, finite.
+ *   p           host; copied.  NULL is ITPP_ERR_ARG.
+ *   cuda_stream cudaStream_t to run on (NULL = the legacy default stream).
+ *   out         receives the handle; untouched on error.
+ * Errors: ITPP_ERR_ARG (bad sizes, bits >= n, delta < 0, cap_M == 0,
+ * non-finite alpha or dtau), ITPP_ERR_ALLOC, ITPP_ERR_CUDA. */
+itpp_status itpp_create(int n, const uint64_t* gate_x, const uint64_t* gate_z,
+                        const double* alpha, int n_gates, double dtau,
+                        const itpp_params* p, void* cuda_stream, itpp_handle* out);
+
+/* Free every device and host resource of the handle (synchronises its
+ * stream first).  NULL is accepted. */
+itpp_status itpp_destroy(itpp_handle h);
+
+/* ---------------------------------------------------------------------------
+ * The hot path
+ * ------------------------------------------------------------------------- */
+
+/* Apply n_layers Trotter layers (Algorithm 1, loop over Trotter steps): for
+ * every gate in order, each term P with coefficient c becomes
+ *   P (coefficient c)                              if {P, Q} = 0,
+ *   cosh(theta) c P  and  -sinh(theta) c (Q P)     if [P, Q] = 0
+ * (Eq. (ITPP_PropRules), derived in App. A), where Q P = s R with s = +-1 and
+ * R the string (xQ^xP, zQ^zP); children with the same string are summed
+ * (Algorithm 1, "Accumulate"), terms with |c| <= delta are dropped, the cap
+ * policy is applied, and every coefficient is divided by the identity's
+ * ("Truncate and normalize", Sec. II.C per-step trace normalisation).
+ * Asynchronous.  n_layers >= 0. */
+itpp_status itpp_apply_trotter_layer(itpp_handle h, int n_layers);
+
+/* Apply the single gate k (0 <= k < n_gates) of the Trotter order; the same
+ * elementary step as inside itpp_apply_trotter_layer.  Asynchronous. */
+itpp_status itpp_apply_gate(itpp_handle h, int k);
+
+/* Threshold truncation of the current (normalised) state: keep |c| > delta,
+ * then renormalise (Sec. II.B "Coefficient threshold"; Algorithm 1
+ * "Truncate and normalize").  delta >= 0; a delta >= 1 would drop the
+ * identity and is ITPP_ERR_TRACE_ZERO.  Asynchronous. */
+itpp_status itpp_truncate(itpp_handle h, double delta);
+
+/* Expectation value <O> = Tr[O rho] / Tr[rho] = sum_j w_j c_{P_j} of
+ * O = sum_j w_j P_j (Sec. II.C, expectation from the propagated operator;
+ * Tr(P_a P_b) = 2^n delta_ab and the identity coefficient is one).
+ *   obs_x/z  host, m * W words; obs_w host, m weights; 1 <= m <= 65536.
+ *   out      host; receives <O>.
+ * Synchronising.  The sum over j is compensated (Kahan). */
+itpp_status itpp_expect(itpp_handle h, const uint64_t* obs_x, const uint64_t* obs_z,
+                        const double* obs_w, int m, double* out);
+
+/* The coefficient c_{P_j} of each string (0 where the string is absent).
+ * Host arrays; out has m entries.  Synchronising. */
+itpp_status itpp_coeffs(itpp_handle h, const uint64_t* obs_x, const uint64_t* obs_z,
+                        int m, double* out);
+
+/* Device-pointer form of itpp_coeffs + itpp_expect, fully asynchronous:
+ * d_obs_x/z (m*W words), d_obs_w (m) and d_out (m+1 doubles: the m
+ * coefficients, then the weighted sum) are device memory that must stay valid
+ * until the stream reaches the work. */
+itpp_status itpp_expect_device(itpp_handle h, const uint64_t* d_obs_x, const uint64_t* d_obs_z,
+                               const double* d_obs_w, int m, double* d_out);
+
+/* ---------------------------------------------------------------------------
+ * State access
+ * ------------------------------------------------------------------------- */
+
+/* Wait for the stream and return the handle's status. */
+itpp_status itpp_synchronize(itpp_handle h);
+
+/* Current number of terms.  Synchronising. */
+itpp_status itpp_get_count(itpp_handle h, uint64_t* count);
+
+/* Copy the current normalised state to host buffers x, z (capacity * W words
+ * each) and c (capacity doubles).  The order of the terms is unspecified.
+ * *count receives the term count; ITPP_ERR_CAPACITY if capacity < count
+ * (nothing copied).  Synchronising. */
+itpp_status itpp_get_terms(itpp_handle h, uint64_t* x, uint64_t* z, double* c,
+                           uint64_t capacity, uint64_t* count);
+
+/* Replace the state by count terms from host buffers (checkpoint resume,
+ * synthetic states).  Keys must be distinct, bits >= n zero, and the
+ * identity must be present with a nonzero coefficient; count <= cap_M.
+ * Clears the stored device status.  Synchronising. */
+itpp_status itpp_set_terms(itpp_handle h, const uint64_t* x, const uint64_t* z,
+                           const double* c, uint64_t count);
+
+/* Device counters (see itpp_stats).  Synchronising. */
+itpp_status itpp_get_stats(itpp_handle h, itpp_stats* out);
+
+/* Kernel timing with CUDA events recorded on the handle's stream around the
+ * launches of the gate kernels.  itpp_profile_enable(h, 1) starts (and
+ * clears) the accumulation; itpp_profile_read synchronises and returns, for
+ * kernel class kid (0 = merge-table build, 1 = branch-emit-merge-truncate,
+ * 2 = cap select, 3 = expectation), the number of launches and their total
+ * device time in milliseconds. */
+itpp_status itpp_profile_enable(itpp_handle h, int enable);
+itpp_status itpp_profile_read(itpp_handle h, int kid, uint64_t* launches, double* total_ms);
+
+/* Human-readable name of a status code (static storage). */
+const char* itpp_status_string(itpp_status s);
+
+/* Library version, e.g. "itpp-gb300 0.1". */
+const char* itpp_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* ITPP_H */

@@ -1,0 +1,63 @@
+// itpp_launch.h -- host-side launchers of the sm_103a kernels (internal).
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace itpp {
+
+struct DevCtl;
+
+// Device resources of one propagation (or of one batch instance table).
+struct DeviceState {
+    int n = 0, W = 1;
+    void* keys[2] = {nullptr, nullptr};   // PKey<W>[buf_cap]
+    double* coef[2] = {nullptr, nullptr}; // double[buf_cap]
+    void* table = nullptr;                // Slot<W>[table_slots]
+    uint64_t table_slots = 0;
+    DevCtl* ctl = nullptr;
+    uint64_t cap_M = 0, buf_cap = 0;
+    int cap_policy = 0;
+    double delta = 0;
+    // launch shape
+    int num_sms = 1;
+    int block = 256, ipt = 2, load_pct = 50, probe_limit = 4096;
+};
+
+// Per-gate host constants (computed once in itpp_create).
+struct HostGate {
+    uint64_t qx[2] = {0, 0}, qz[2] = {0, 0};
+    double ch = 1, msh = 0;  // cosh(theta), -sinh(theta)
+    double sh = 0, chd = 1;  // d ch / d theta = sinh(theta), -d msh / d theta = cosh(theta)
+    int qyy = 0;
+};
+
+// One elementary gate: merge-table build, branch-emit-merge-truncate, post.
+cudaError_t launch_gate_insert(const DeviceState& s, const HostGate& g, cudaStream_t st);
+cudaError_t launch_gate_main(const DeviceState& s, const HostGate& g, cudaStream_t st);
+cudaError_t launch_gate_post(const DeviceState& s, cudaStream_t st);
+// Top-M select and compaction (no-ops on the device when the bound holds).
+cudaError_t launch_cap(const DeviceState& s, cudaStream_t st);
+int cap_launches(const DeviceState& s);
+// Sort-based merge path (children buffer, radix sort, segmented reduce).
+cudaError_t launch_gate_sorted(const DeviceState& s, const HostGate& g, void* scratch,
+                               uint64_t scratch_bytes, cudaStream_t st);
+uint64_t sorted_scratch_bytes(int W, uint64_t buf_cap);
+
+// Expectation: obs table build, state scan, reduction.  d_tab holds
+// tsize ints, d_first m ints, d_vals m doubles.
+cudaError_t launch_expect(const DeviceState& s, const uint64_t* d_ox, const uint64_t* d_oz,
+                          const double* d_ow, int m, int tsize, int* d_tab, int* d_first,
+                          double* d_vals, double* d_out, cudaStream_t st);
+// Normalised export into the other buffer's memory: x plane, z plane, c.
+cudaError_t launch_export(const DeviceState& s, uint64_t* d_x, uint64_t* d_z, double* d_c,
+                          cudaStream_t st);
+// Import from x/z planes and c into buffer 0, with bit and duplicate checks.
+cudaError_t launch_import(const DeviceState& s, const uint64_t* d_x, const uint64_t* d_z,
+                          const double* d_c, uint64_t count, cudaStream_t st);
+// Explicit threshold truncation + normalisation of the current state.
+cudaError_t launch_truncate(const DeviceState& s, double delta, cudaStream_t st);
+// Reset the control block (state = identity in buffer 0).
+cudaError_t launch_reset_identity(const DeviceState& s, cudaStream_t st);
+
+}  // namespace itpp

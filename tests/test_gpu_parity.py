@@ -1,0 +1,272 @@
+"""GPU path vs the CPU oracle, element by element, through the C ABI.
+
+Bar: string sets identical and coefficients identical in every bit (the
+merge has at most two addends per string, so the GPU and the oracle round
+the same operations); observables within 1e-10 of the oracle relative to
+sum_j |w_j c_j| (the sums are ordered differently).
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+import workloads as wl
+from tests._compare import assert_same_state, rel_close
+
+pytestmark = pytest.mark.gpu
+
+itpp = pytest.importorskip("paper_2601_14400_gb300")
+
+
+def _pair(H, dtau, delta, cap_M=1 << 16, cap_policy=0, **kw):
+    g = itpp.Propagator(H.n, H.gate_x, H.gate_z, H.alpha, dtau, delta, cap_M, cap_policy, **kw)
+    o = oracle.Oracle(H.n, H.gate_x, H.gate_z, H.alpha, dtau, delta, cap_M, cap_policy)
+    return g, o
+
+
+def _obs_check(g, o, obs):
+    got = g.expect(obs)
+    want = o.expect(obs)
+    cs = o.coeffs(obs.x, obs.z)
+    scale = float(np.sum(np.abs(obs.w * cs)))
+    assert rel_close(got, want, 1e-10, scale), (got, want)
+    gc = g.coeffs(obs.x, obs.z)
+    assert np.array_equal(gc.view(np.uint64), cs.view(np.uint64))
+
+
+# ---------------------------------------------------------------------------
+# The n = 8 chain workload, in full, with per-layer observables
+# ---------------------------------------------------------------------------
+def test_tfim_n8_full_run_bit_exact():
+    w = wl.WORKLOADS["tfim1d_n8_open"]
+    g, o = _pair(w.H, w.dtau, w.delta, w.cap_M, w.cap_policy)
+    for layer in range(w.n_layers):
+        g.apply_trotter_layer(1)
+        o.apply_layers(1)
+        assert_same_state(g.terms(), o.terms(), f"layer {layer}")
+        for name, obs in w.observables.items():
+            _obs_check(g, o, obs)
+    st = g.stats()
+    assert st["gates_applied"] == w.n_layers * w.H.n_gates
+
+
+@pytest.mark.parametrize("k_steps", [1, 2, 3, 15, 16, 40])
+def test_single_gates_bit_exact(k_steps):
+    H = wl.tfim_1d(6, 1.0, 0.7, periodic=True)
+    g, o = _pair(H, 0.1, 1e-9)
+    for s in range(k_steps):
+        k = s % H.n_gates
+        g.apply_gate(k)
+        o.apply_gate(k)
+    assert_same_state(g.terms(), o.terms(), f"after {k_steps} gates")
+
+
+# ---------------------------------------------------------------------------
+# General Pauli Hamiltonians and word boundaries (W = 1 and 2)
+# ---------------------------------------------------------------------------
+@pytest.mark.parametrize("n,terms,seed,layers,delta", [
+    (10, 12, 1, 3, 1e-6), (33, 20, 2, 2, 1e-5), (64, 24, 3, 2, 1e-5),
+    (65, 24, 4, 2, 1e-5), (100, 30, 5, 2, 1e-4), (128, 30, 6, 2, 1e-4)])
+def test_random_hamiltonian_bit_exact(n, terms, seed, layers, delta):
+    H = wl.random_pauli_hamiltonian(n, terms, seed, max_weight=4)
+    g, o = _pair(H, 0.15, delta, cap_M=1 << 18)
+    for layer in range(layers):
+        g.apply_trotter_layer(1)
+        o.apply_layers(1)
+        assert_same_state(g.terms(), o.terms(), f"n={n} layer {layer}")
+
+
+@pytest.mark.parametrize("n", [1, 2, 63, 64, 65, 127, 128])
+def test_tfim_word_boundaries(n):
+    periodic = n >= 3
+    H = wl.tfim_1d(n, 1.0, 1.0, periodic=periodic)
+    g, o = _pair(H, 0.05, 2e-3, cap_M=1 << 18)
+    g.apply_trotter_layer(2)
+    o.apply_layers(2)
+    assert_same_state(g.terms(), o.terms(), f"n={n}")
+    _obs_check(g, o, wl.energy_observable(H))
+
+
+def test_tfim_2d_prefix_bit_exact():
+    H = wl.tfim_2d(5, 1.0, 3.04)     # n = 25
+    g, o = _pair(H, 0.02, 1e-4, cap_M=1 << 20)
+    for layer in range(2):
+        g.apply_trotter_layer(1)
+        o.apply_layers(1)
+    assert_same_state(g.terms(), o.terms(), "2d")
+    _obs_check(g, o, wl.energy_observable(H))
+
+
+def test_tfim_11x11_gate_prefix_bit_exact():
+    # the 11x11 workload itself (W = 2): all 220 bonds and the first fields
+    w = wl.WORKLOADS["tfim2d_11x11"]
+    g, o = _pair(w.H, w.dtau, w.delta, cap_M=1 << 22)
+    for k in range(236):
+        g.apply_gate(k)
+        o.apply_gate(k)
+    assert_same_state(g.terms(), o.terms(), "11x11")
+    for obs in w.observables.values():
+        _obs_check(g, o, obs)
+
+
+# ---------------------------------------------------------------------------
+# Synthetic states spanning many tiles with a ragged tail, one gate each
+# ---------------------------------------------------------------------------
+@pytest.mark.parametrize("n,M", [(64, (1 << 15) + 77), (121, (1 << 14) + 5), (20, 3001)])
+@pytest.mark.parametrize("which", ["zz", "x", "y"])
+def test_synthetic_state_one_gate(n, M, which):
+    X, Z, C = wl.synthetic_state(n, M, 2601 + n, delta=1e-6)
+    if which == "zz":
+        gx, gz = wl.two_site(n, 3, 4, "Z", "Z")
+    elif which == "x":
+        gx, gz = wl.single_site(n, 5, "X")
+    else:
+        gx, gz = wl.two_site(n, 0, n - 1, "Y", "X")
+    H = wl.Hamiltonian(n, gx[None], gz[None], np.array([-0.7]))
+    g, o = _pair(H, 0.05, 1e-6, cap_M=M + 1)
+    g.set_terms(X, Z, C)
+    o.set_terms(X, Z, C)
+    assert_same_state(g.terms(), o.terms(), "loaded")
+    g.apply_gate(0)
+    o.apply_gate(0)
+    assert_same_state(g.terms(), o.terms(), f"{which} gate")
+
+
+# ---------------------------------------------------------------------------
+# Edge cases and degenerate inputs
+# ---------------------------------------------------------------------------
+def test_identity_only_and_delta_zero():
+    H = wl.tfim_1d(4, 1.0, 1.0)
+    g, o = _pair(H, 0.1, 0.0)
+    assert g.count() == 1
+    x, z, c = g.terms()
+    assert c[0] == 1.0 and not x.any() and not z.any()
+    g.apply_trotter_layer(3)
+    o.apply_layers(3)
+    assert_same_state(g.terms(), o.terms(), "delta=0")
+
+
+def test_everything_truncated_but_identity():
+    H = wl.tfim_1d(5, 1.0, 1.0)
+    g, o = _pair(H, 0.05, 0.5)
+    g.apply_trotter_layer(4)
+    o.apply_layers(4)
+    assert g.count() == 1
+    assert_same_state(g.terms(), o.terms(), "delta=0.5")
+
+
+def test_explicit_truncate():
+    w = wl.WORKLOADS["tfim1d_n8_open"]
+    g, o = _pair(w.H, w.dtau, 0.0)
+    g.apply_trotter_layer(5)
+    o.apply_layers(5)
+    g.truncate(1e-3)
+    x, z, c = o.terms()
+    keep = np.abs(c) > 1e-3
+    assert_same_state(g.terms(), (x[keep], z[keep], c[keep]), "truncate")
+    with pytest.raises(itpp.ItppError):
+        g.truncate(2.0)      # would drop the identity
+        g.synchronize()
+
+
+def test_cap_policy_error():
+    H = wl.tfim_1d(8, 1.0, 1.0)
+    g = itpp.Propagator(H.n, H.gate_x, H.gate_z, H.alpha, 0.1, 1e-9, 50, 0)
+    with pytest.raises(itpp.ItppError) as e:
+        g.apply_trotter_layer(3)
+        g.synchronize()
+    assert e.value.status == 3
+    with pytest.raises(itpp.ItppError):
+        g.count()
+
+
+@pytest.mark.parametrize("M", [100, 1000, 2049])
+def test_cap_policy_topM_bit_exact(M):
+    H = wl.tfim_1d(10, 1.0, 1.0, periodic=True)
+    g, o = _pair(H, 0.1, 1e-9, cap_M=M, cap_policy=1)
+    for layer in range(4):
+        g.apply_trotter_layer(1)
+        o.apply_layers(1)
+        assert_same_state(g.terms(), o.terms(), f"M={M} layer {layer}")
+    assert g.stats()["cap_events"] > 0
+
+
+def test_cap_policy_topM_with_exact_ties():
+    n, M = 16, 500
+    X, Z, C = wl.synthetic_state(n, 2000, 9, delta=1e-3)
+    C[1:] = np.sign(C[1:]) * 2.0 ** np.round(np.log2(np.abs(C[1:])))   # many equal |c|
+    gx, gz = wl.single_site(n, 2, "X")
+    H = wl.Hamiltonian(n, gx[None], gz[None], np.array([-1.0]))
+    g, o = _pair(H, 0.1, 1e-9, cap_M=M, cap_policy=1)
+    g.set_terms(X[:M], Z[:M], C[:M])
+    o.set_terms(X[:M], Z[:M], C[:M])
+    g.apply_gate(0)
+    o.apply_gate(0)
+    assert_same_state(g.terms(), o.terms(), "ties")
+
+
+def test_set_terms_validation():
+    H = wl.tfim_1d(8, 1.0, 1.0)
+    g = itpp.Propagator(H.n, H.gate_x, H.gate_z, H.alpha, 0.1, 1e-9, 1000, 0)
+    X, Z, C = wl.synthetic_state(8, 20, 1)
+    with pytest.raises(itpp.ItppError) as e:      # duplicate key
+        g.set_terms(np.concatenate([X, X[3:4]]), np.concatenate([Z, Z[3:4]]),
+                    np.concatenate([C, C[3:4]]))
+    assert e.value.status == 1
+    with pytest.raises(itpp.ItppError) as e:      # identity missing
+        g.set_terms(X[1:], Z[1:], C[1:])
+    assert e.value.status == 6
+    Xb = X.copy()
+    Xb[2, 0] |= np.uint64(1) << np.uint64(9)       # bit >= n
+    with pytest.raises(itpp.ItppError) as e:
+        g.set_terms(Xb, Z, C)
+    assert e.value.status == 1
+    g.set_terms(X, Z, C)                          # still usable afterwards
+    assert g.count() == 21
+
+
+def test_create_validation():
+    H = wl.tfim_1d(8, 1.0, 1.0)
+    bad = H.gate_x.copy()
+    bad[0, 0] |= np.uint64(1) << np.uint64(40)
+    for args in [dict(delta=-1.0), dict(cap_M=0), dict(cap_policy=3)]:
+        kw = dict(delta=1e-6, cap_M=100, cap_policy=0)
+        kw.update(args)
+        with pytest.raises(itpp.ItppError):
+            itpp.Propagator(8, H.gate_x, H.gate_z, H.alpha, 0.1, kw["delta"], kw["cap_M"],
+                            kw["cap_policy"])
+    with pytest.raises(itpp.ItppError):
+        itpp.Propagator(8, bad, H.gate_z, H.alpha, 0.1, 1e-6, 100)
+
+
+@pytest.mark.parametrize("block,ipt,load", [(128, 1, 25), (256, 4, 75), (512, 2, 50)])
+def test_launch_shapes_give_identical_states(block, ipt, load):
+    H = wl.tfim_1d(12, 1.0, 1.0, periodic=True)
+    g, o = _pair(H, 0.05, 1e-7, cap_M=1 << 18, block_threads=block, items_per_thread=ipt,
+                 table_load_pct=load)
+    g.apply_trotter_layer(3)
+    o.apply_layers(3)
+    assert_same_state(g.terms(), o.terms(), f"block={block} ipt={ipt} load={load}")
+
+
+# ---------------------------------------------------------------------------
+# The paper's printed count: untruncated N = 12 support
+# ---------------------------------------------------------------------------
+def test_paper_untruncated_support_n12():
+    import json, os
+    gold = json.load(open(os.path.join(os.path.dirname(__file__), "golden",
+                                       "paper_numbers.json")))["untruncated_support_N12"]
+    H = wl.tfim_1d(12, 1.0, 0.5)
+    g = itpp.Propagator(12, H.gate_x, H.gate_z, H.alpha, 0.04, 0.0, 1 << 22)
+    prev = -1
+    for layer in range(500):        # tau = 20
+        g.apply_trotter_layer(10)
+        c = g.count()
+        if c == prev:
+            break
+        prev = c
+    assert g.count() == gold["value"]
+    x, z, c = g.terms()
+    ident = ~(x.any(axis=1) | z.any(axis=1))
+    assert ident.sum() == 1 and c[ident][0] == 1.0

@@ -337,9 +337,10 @@ def _build_workloads():
     for o in zz_observables(121, [(c, c + 1), (c, c + 11)]):
         obs2[o.labels[0]] = o
     w["tfim2d_11x11"] = Workload(
-        "tfim2d_11x11", H2, 0.02, 30, 1e-5, 1 << 26, 0, obs2,
+        "tfim2d_11x11", H2, 0.02, 30, 1e-5, 1 << 28, 1, obs2,
         "11x11 open square lattice, J=1, h=3.04, dtau=0.02, 30 layers (beta=0.6), "
-        "|c|<=1e-5 dropped")
+        "|c|<=1e-5 dropped; the threshold alone exceeds 2^29 terms by the third "
+        "layer, so at most 2^28 terms are kept (top-M)")
     Ha = adjoint_chain()
     obsa = {"energy": energy_observable(Ha)}
     for o in zz_observables(32, [(15, 16)]):
