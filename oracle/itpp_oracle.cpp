@@ -23,7 +23,9 @@
 //                                truncate |c| > delta (Sec. II.B), cap (the
 //                                term bound of the "Practical considerations"
 //                                paragraph, Sec. II.C), normalise by the
-//                                identity coefficient (Sec. II.C).
+//                                identity coefficient: identify it and
+//                                rescale every coefficient by its reciprocal
+//                                (Sec. II.C).
 //   expect ...................... <O> = Tr[O rho] with the identity
 //                                coefficient equal to one (Sec. II.C, the
 //                                expectation from the propagated operator).
@@ -153,9 +155,12 @@ int apply_gate(Oracle& o, int k) {
         for (auto& kv : v) next.insert(kv);
         if (next.find(I) == next.end()) return ERR_TRACE_ZERO;
     }
-    // normalise by the trace: divide by the identity coefficient
+    // normalise by the trace: rescale every coefficient by the reciprocal of
+    // the identity coefficient (one division per step), the identity itself
+    // becoming exactly one
     const double cI = next[I];
-    for (auto& kv : next) kv.second = kv.second / cI;
+    const double inv = 1.0 / cI;
+    for (auto& kv : next) kv.second = kv.first.is_identity() ? 1.0 : kv.second * inv;
     o.rho.swap(next);
     if (o.record) {
         std::vector<Key> s;

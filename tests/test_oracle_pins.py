@@ -219,7 +219,8 @@ def test_threshold_strict_and_before_normalisation():
         key = (int(xA[0]), int(zA[0]))
         assert (key in d) == present
         if present:
-            assert d[key] == a / math.cosh(-1.0 * 0.1)   # normalised afterwards
+            # normalised afterwards: rescaled by the reciprocal of c_I = cosh
+            assert d[key] == a * (1.0 / math.cosh(-1.0 * 0.1))
 
 
 def test_cap_keeps_largest_with_key_tiebreak():
