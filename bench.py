@@ -56,7 +56,7 @@ def parse():
                     help="untimed layers before warm-up (-1: until the bound is reached)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
-    ap.add_argument("--ref-gates", type=int, default=160,
+    ap.add_argument("--ref-gates", type=int, default=224,
                     help="oracle gates per reference step (bounded CPU sample)")
     return ap.parse_args()
 

@@ -78,7 +78,7 @@ k_obs_scan(BufsA<W> B, DevCtl* ctl, const uint64_t* __restrict__ ox,
            double* vals) {
     const int cur = ctl->cur;
     const uint64_t n = live_count(ctl, cur);
-    const double norm = ctl->norm[cur];
+    const double rnorm = ctl->rnorm[cur];
     const uint64_t mask = (uint64_t)tsize - 1;
     for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
          i += (uint64_t)gridDim.x * blockDim.x) {
@@ -88,7 +88,7 @@ k_obs_scan(BufsA<W> B, DevCtl* ctl, const uint64_t* __restrict__ ox,
             const int e = __ldg(tab + h);
             if (e < 0) break;
             if (key_eq(key_from_planes<W>(ox, oz, (uint64_t)e), K)) {
-                vals[e] = __ddiv_rn(__ldg(B.c[cur] + i), norm);
+                vals[e] = normalised(__ldg(B.c[cur] + i), rnorm, key_is_zero(K));
                 break;
             }
             h = (h + 1) & mask;
@@ -158,13 +158,13 @@ __global__ void __launch_bounds__(256)
 k_export(BufsA<W> B, const DevCtl* ctl, uint64_t* xo, uint64_t* zo, double* co) {
     const int cur = ctl->cur;
     const uint64_t n = live_count(ctl, cur);
-    const double norm = ctl->norm[cur];
+    const double rnorm = ctl->rnorm[cur];
     for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
          i += (uint64_t)gridDim.x * blockDim.x) {
         const PKey<W> K = load_key(B.k[cur] + i);
 #pragma unroll
         for (int w = 0; w < W; ++w) { xo[i * W + w] = K.x[w]; zo[i * W + w] = K.z[w]; }
-        co[i] = __ddiv_rn(B.c[cur][i], norm);
+        co[i] = normalised(B.c[cur][i], rnorm, key_is_zero(K));
     }
 }
 
@@ -187,6 +187,8 @@ __global__ void k_import_begin(DevCtl* ctl, uint64_t count) {
         ctl->count[1] = 0;
         ctl->norm[0] = 1.0;
         ctl->norm[1] = 1.0;
+        ctl->rnorm[0] = 1.0;
+        ctl->rnorm[1] = 1.0;
         ctl->status = 0;
         ctl->err_info = 0;
         ctl->gen = ctl->gen + 1u;
@@ -316,6 +318,8 @@ __global__ void k_reset_identity(BufsA<W> B, DevCtl* ctl) {
         ctl->count[1] = 0;
         ctl->norm[0] = 1.0;
         ctl->norm[1] = 1.0;
+        ctl->rnorm[0] = 1.0;
+        ctl->rnorm[1] = 1.0;
         ctl->status = 0;
         ctl->err_info = 0;
         ctl->gen = ctl->gen + 1u;
@@ -343,6 +347,7 @@ __global__ void k_trunc_begin(DevCtl* ctl) {
         const int cur = ctl->cur;
         ctl->count[cur ^ 1] = 0;
         ctl->norm[cur ^ 1] = 1.0;
+        ctl->rnorm[cur ^ 1] = 1.0;
     }
 }
 
@@ -354,7 +359,7 @@ k_trunc(BufsA<W> B, DevCtl* ctl, double delta) {
     if (ctl->status) return;
     const int cur = ctl->cur;
     const uint64_t n = live_count(ctl, cur);
-    const double norm = ctl->norm[cur];
+    const double rnorm = ctl->rnorm[cur];
     const uint64_t tiles = (n + BLOCK - 1) / BLOCK;
     for (uint64_t t = blockIdx.x; t < tiles; t += gridDim.x) {
         const uint64_t i = t * BLOCK + threadIdx.x;
@@ -363,7 +368,7 @@ k_trunc(BufsA<W> B, DevCtl* ctl, double delta) {
         bool keep = false;
         if (i < n) {
             K = load_key_stream(B.k[cur] + i);
-            c = __ddiv_rn(__ldcs(B.c[cur] + i), norm);
+            c = normalised(__ldcs(B.c[cur] + i), rnorm, key_is_zero(K));
             keep = fabs(c) > delta;
             if (key_is_zero(K) && !keep) {
                 set_status(ctl, ST_TRACE_ZERO, 20);

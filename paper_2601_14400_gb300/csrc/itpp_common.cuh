@@ -7,8 +7,10 @@
 //     coef  double[2*cap_M]   raw (un-normalised) coefficients
 //   merge table  Slot<W>[2^t]  open addressing, 32 B (W=1) / 64 B (W=2) slots
 //   DevCtl       counters, the current-buffer index, normalisers, status
-// The stored coefficient of term i is raw[i]; its value is raw[i] / norm[cur]
-// (the trace normalisation of Sec. II.C, applied when the term is next read).
+// The stored coefficient of term i is raw[i]; its value is raw[i] * rnorm[cur]
+// with rnorm = 1 / (raw identity coefficient), and exactly 1 for the identity
+// (the trace normalisation of Sec. II.C -- identify the identity coefficient
+// and rescale every coefficient -- applied when the term is next read).
 #pragma once
 
 #include <cstdint>
@@ -62,7 +64,8 @@ constexpr int kTieBins = 1 << kTieBits;
 struct DevCtl {
     unsigned long long count[2];   // term count of state buffer 0 / 1
     unsigned long long buf_cap;    // capacity of each state buffer (terms)
-    double norm[2];                // normaliser of buffer 0 / 1
+    double norm[2];                // normaliser of buffer 0 / 1 (raw identity coefficient)
+    double rnorm[2];               // its reciprocal, 1.0 / norm (one division per gate)
     int cur;                       // buffer holding the state
     int status;                    // first device error (ST_*), sticky
     unsigned int gen;              // merge-table generation of the current gate
@@ -92,6 +95,11 @@ struct DevCtl {
 __device__ __forceinline__ uint64_t live_count(const DevCtl* ctl, int b) {
     const unsigned long long n = ctl->count[b];
     return n < ctl->buf_cap ? n : ctl->buf_cap;
+}
+
+// Normalised value of a stored coefficient.
+__device__ __forceinline__ double normalised(double raw, double rnorm, bool identity) {
+    return identity ? 1.0 : __dmul_rn(raw, rnorm);
 }
 
 __device__ __forceinline__ void set_status(DevCtl* ctl, int code, unsigned int info = 0) {

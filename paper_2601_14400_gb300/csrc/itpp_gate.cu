@@ -166,7 +166,7 @@ k_gate_main(Bufs<W> B, DevCtl* ctl, const Slot<W>* __restrict__ table, uint64_t 
     if (ctl->status) return;
     const int cur = ctl->cur;
     const uint64_t n = live_count(ctl, cur);
-    const double norm = ctl->norm[cur];
+    const double rnorm = ctl->rnorm[cur];
     const unsigned gen = ctl->gen;
     const uint64_t mask = table_mask(n, alloc_slots, load_pct);
     const PKey<W>* __restrict__ kin = B.k[cur];
@@ -191,8 +191,8 @@ k_gate_main(Bufs<W> B, DevCtl* ctl, const Slot<W>* __restrict__ table, uint64_t 
             for (int w = 0; w < W; ++w) { K[j].x[w] = 0; K[j].z[w] = 0; }
             if (i < n) {
                 K[j] = load_key_stream(kin + i);
-                // normalise on load: the previous gate's trace division
-                const double c = __ddiv_rn(__ldcs(cin + i), norm);
+                // normalise on load: the previous gate's trace rescaling
+                const double c = normalised(__ldcs(cin + i), rnorm, key_is_zero(K[j]));
                 bool keep_b = false;
                 if (!commutes(K[j], g)) {
                     va[j] = c;                                   // {P,Q} = 0: unchanged
@@ -201,7 +201,7 @@ k_gate_main(Bufs<W> B, DevCtl* ctl, const Slot<W>* __restrict__ table, uint64_t 
                     const PKey<W> P = key_xor(K[j], g);
                     double cp_raw;
                     if (table_find(table, mask, gen, P, &cp_raw, probe_limit, ctl, &probes)) {
-                        const double cp = __ddiv_rn(cp_raw, norm);
+                        const double cp = normalised(cp_raw, rnorm, key_is_zero(P));
                         va[j] = __dadd_rn(__dmul_rn(c, g.ch), __dmul_rn(cp, m));
                     } else {
                         va[j] = __dmul_rn(c, g.ch);              // cosh(theta) P
@@ -260,6 +260,7 @@ __global__ void k_gate_post(DevCtl* ctl, uint64_t cap_M, int cap_policy) {
         const int cur = ctl->cur, nxt = cur ^ 1;
         const unsigned long long n_in = ctl->count[cur], n_out = ctl->count[nxt];
         ctl->cur = nxt;
+        ctl->rnorm[nxt] = __ddiv_rn(1.0, ctl->norm[nxt]);
         ctl->gen = ctl->gen + 1u;
         if (ctl->gen == 0u) set_status(ctl, ST_STATE, 1);   // generation counter wrapped
         ctl->stat_gates += 1;
@@ -394,6 +395,7 @@ k_cap_ties(Bufs<W> B, DevCtl* ctl, PKey<W>* tie_list) {
     if (blockIdx.x == 0 && threadIdx.x == 0) {
         ctl->count[cur ^ 1] = 0ULL;
         ctl->norm[cur ^ 1] = ctl->norm[cur];
+        ctl->rnorm[cur ^ 1] = ctl->rnorm[cur];
     }
     if (ctl->sel_k == ctl->sel_ties) return;   // every tie is kept
     const uint64_t n = live_count(ctl, cur);

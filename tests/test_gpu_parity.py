@@ -124,7 +124,7 @@ def test_synthetic_state_one_gate(n, M, which):
     else:
         gx, gz = wl.two_site(n, 0, n - 1, "Y", "X")
     H = wl.Hamiltonian(n, gx[None], gz[None], np.array([-0.7]))
-    g, o = _pair(H, 0.05, 1e-6, cap_M=M + 1)
+    g, o = _pair(H, 0.05, 1e-6, cap_M=2 * M + 2)
     g.set_terms(X, Z, C)
     o.set_terms(X, Z, C)
     assert_same_state(g.terms(), o.terms(), "loaded")
