@@ -358,6 +358,7 @@ def main():
             "cpu_baseline": cpu,
             "gpu_launches": int(launches),
             "timed_gates": int(gates),
+            "table_probes_per_term": (st1["table_probes"] - st0["table_probes"]) / max(terms_in, 1),
             "terms_in_timed": int(terms_in),
         }
         print(json.dumps(line), flush=True)

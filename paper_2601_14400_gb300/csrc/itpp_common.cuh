@@ -97,6 +97,14 @@ __device__ __forceinline__ uint64_t live_count(const DevCtl* ctl, int b) {
     return n < ctl->buf_cap ? n : ctl->buf_cap;
 }
 
+// |c| > delta for delta >= 0, decided on the bit patterns: for non-negative
+// doubles the unsigned order of the patterns is the numeric order, so this is
+// exact (NaN patterns exceed +inf and count as kept, where fabs(c) > delta
+// would drop them; the propagation produces no NaN from finite inputs).
+__device__ __forceinline__ bool above(double c, unsigned long long delta_bits) {
+    return ((unsigned long long)__double_as_longlong(c) & 0x7fffffffffffffffULL) > delta_bits;
+}
+
 // Normalised value of a stored coefficient.
 __device__ __forceinline__ double normalised(double raw, double rnorm, bool identity) {
     return identity ? 1.0 : __dmul_rn(raw, rnorm);

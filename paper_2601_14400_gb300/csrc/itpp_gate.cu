@@ -167,6 +167,7 @@ k_gate_main(Bufs<W> B, DevCtl* ctl, const Slot<W>* __restrict__ table, uint64_t 
     const int cur = ctl->cur;
     const uint64_t n = live_count(ctl, cur);
     const double rnorm = ctl->rnorm[cur];
+    const unsigned long long dbits = (unsigned long long)__double_as_longlong(delta);
     const unsigned gen = ctl->gen;
     const uint64_t mask = table_mask(n, alloc_slots, load_pct);
     const PKey<W>* __restrict__ kin = B.k[cur];
@@ -206,10 +207,10 @@ k_gate_main(Bufs<W> B, DevCtl* ctl, const Slot<W>* __restrict__ table, uint64_t 
                     } else {
                         va[j] = __dmul_rn(c, g.ch);              // cosh(theta) P
                         vb[j] = __dmul_rn(c, m);                 // -sinh(theta) s (Q.P)
-                        keep_b = fabs(vb[j]) > delta;
+                        keep_b = above(vb[j], dbits);
                     }
                 }
-                bool keep_a = fabs(va[j]) > delta;
+                bool keep_a = above(va[j], dbits);
                 if (key_is_zero(K[j])) {
                     // the identity: its merged coefficient is the new trace
                     ctl->norm[cur ^ 1] = va[j];
