@@ -211,6 +211,53 @@ itpp_status itpp_get_stats(itpp_handle h, itpp_stats* out);
 itpp_status itpp_profile_enable(itpp_handle h, int enable);
 itpp_status itpp_profile_read(itpp_handle h, int kid, uint64_t* launches, double* total_ms);
 
+/* ---------------------------------------------------------------------------
+ * One gate without device allocation
+ * ------------------------------------------------------------------------- */
+
+/* Largest input term count of itpp_gate_apply_noalloc for W = ceil(n/64)
+ * mask words: its merge table is a fixed 16 MiB, filled at most half. */
+#define ITPP_NOALLOC_MAX_TERMS(W) ((W) == 1 ? 262144ULL : 131072ULL)
+
+/* One elementary gate (the same step as itpp_apply_gate: propagate, merge,
+ * truncate |c| > delta, rescale by the identity coefficient) on buffers the
+ * caller owns, allocating nothing.  The paper has no counterpart: this entry
+ * point exists for callers that cannot call cudaMalloc at that point -- code
+ * running inside a memory pool or arena that owns all device memory, or a
+ * host path that must not pay the implicit synchronisation of cudaMalloc /
+ * cudaFree.  Its scratch (merge table and control block, about 17 MiB) is a
+ * file-scope device array that every GPU loading the library holds until the
+ * process exits; no cudaMalloc, cudaFree or allocating library routine is
+ * called.
+ *   n, gate_x, gate_z  sites and the gate string Q (host, W words each).
+ *   alpha, dtau        Q's coefficient and the step: theta = alpha * dtau.
+ *   delta              threshold (>= 0).
+ *   d_keys_in          device, n_in terms, each 2W words: x[0..W-1] then
+ *                      z[0..W-1]; distinct strings, the identity present.
+ *   d_coef_in          device, n_in normalised coefficients (the identity's
+ *                      is taken as exactly one).
+ *   n_in               1 .. ITPP_NOALLOC_MAX_TERMS(W); larger is
+ *                      ITPP_ERR_CAPACITY.
+ *   d_keys_out/_coef_out  device, room for out_capacity >= 2 * n_in terms
+ *                      (smaller is ITPP_ERR_CAPACITY); receive the kept terms
+ *                      in an unspecified order, normalised.
+ *   d_n_out            device, receives the kept count, or UINT64_MAX when a
+ *                      device-side error (merge-table probe limit, identity
+ *                      truncated) occurred.
+ *   d_trace_out        device or NULL: the identity coefficient before the
+ *                      rescaling.
+ *   cuda_stream        stream to run on.
+ * Asynchronous.  The first call on a device looks up the scratch's device
+ * address (cudaGetSymbolAddress) with that device current; make that first
+ * call before any stream capture.  All calls share the scratch: calls whose
+ * work overlaps on the GPU race and corrupt each other; serialise them. */
+itpp_status itpp_gate_apply_noalloc(int n, const uint64_t* gate_x, const uint64_t* gate_z,
+                                    double alpha, double dtau, double delta,
+                                    const uint64_t* d_keys_in, const double* d_coef_in,
+                                    uint64_t n_in, uint64_t* d_keys_out, double* d_coef_out,
+                                    uint64_t out_capacity, uint64_t* d_n_out,
+                                    double* d_trace_out, void* cuda_stream);
+
 /* Human-readable name of a status code (static storage). */
 const char* itpp_status_string(itpp_status s);
 

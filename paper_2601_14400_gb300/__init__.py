@@ -70,6 +70,10 @@ _SIGNATURES = [
     ("itpp_get_stats", ctypes.c_int, [_vp, ctypes.POINTER(itpp_stats)]),
     ("itpp_profile_enable", ctypes.c_int, [_vp, ctypes.c_int]),
     ("itpp_profile_read", ctypes.c_int, [_vp, ctypes.c_int, _u64p, _f64p]),
+    ("itpp_gate_apply_noalloc", ctypes.c_int, [ctypes.c_int, _u64p, _u64p, ctypes.c_double,
+                                               ctypes.c_double, ctypes.c_double, _vp, _vp,
+                                               ctypes.c_uint64, _vp, _vp, ctypes.c_uint64, _vp,
+                                               _vp, _vp]),
     ("itpp_status_string", ctypes.c_char_p, [ctypes.c_int]),
     ("itpp_version", ctypes.c_char_p, []),
 ]
@@ -98,6 +102,20 @@ def lib():
 def build(force: bool = False) -> str:
     from . import _build
     return _build.build(force=force)
+
+
+def itpp_gate_apply_noalloc(n, gate_x, gate_z, alpha, dtau, delta, d_keys_in, d_coef_in,
+                            n_in, d_keys_out, d_coef_out, out_capacity, d_n_out,
+                            d_trace_out=None, stream=None):
+    """One gate on caller-owned device buffers (integers: device addresses),
+    with no device allocation; see include/itpp.h."""
+    gx, pgx = _u64(gate_x)
+    gz, pgz = _u64(gate_z)
+    st = lib().itpp_gate_apply_noalloc(int(n), pgx, pgz, float(alpha), float(dtau),
+                                       float(delta), d_keys_in, d_coef_in, int(n_in),
+                                       d_keys_out, d_coef_out, int(out_capacity), d_n_out,
+                                       d_trace_out, _stream_ptr(stream))
+    _check(st, "itpp_gate_apply_noalloc")
 
 
 def _u64(a):
