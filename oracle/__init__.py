@@ -57,6 +57,11 @@ def lib():
         L.oracle_coeffs.argtypes = [ctypes.c_void_p, _u64p, _u64p, ctypes.c_int, _f64p]
         L.oracle_expect.restype = ctypes.c_double
         L.oracle_expect.argtypes = [ctypes.c_void_p, _u64p, _u64p, _f64p, ctypes.c_int]
+        L.oracle_record.argtypes = [ctypes.c_void_p, ctypes.c_int]
+        L.oracle_frozen_value.argtypes = [ctypes.c_void_p, _f64p, _u64p, _u64p, _f64p,
+                                          ctypes.c_int, _f64p]
+        L.oracle_adjoint.argtypes = [ctypes.c_void_p, _u64p, _u64p, _f64p, ctypes.c_int,
+                                     _f64p, _f64p]
         L.oracle_commutes.argtypes = [ctypes.c_int, _u64p, _u64p, _u64p, _u64p]
         L.oracle_pauli_product.argtypes = [ctypes.c_int, _u64p, _u64p, _u64p, _u64p,
                                            _u64p, _u64p]
@@ -151,6 +156,36 @@ class Oracle:
         oz, poz = _u64(obs.z)
         ow, pow_ = _f64(obs.w)
         return float(lib().oracle_expect(self._h, pox, poz, pow_, int(ow.shape[0])))
+
+
+class FrozenAdjoint:
+    """Frozen-support forward and its adjoint on top of an Oracle."""
+
+    def __init__(self, o: "Oracle", n_layers: int):
+        self.o = o
+        o._check(lib().oracle_record(o._h, int(n_layers)))
+
+    def value(self, obs, alpha=None):
+        ox, pox = _u64(obs.x)
+        oz, poz = _u64(obs.z)
+        ow, pow_ = _f64(obs.w)
+        f = ctypes.c_double()
+        pa = None
+        if alpha is not None:
+            al, pa = _f64(alpha)
+        self.o._check(lib().oracle_frozen_value(self.o._h, pa, pox, poz, pow_, int(ow.shape[0]),
+                                                ctypes.byref(f)))
+        return f.value
+
+    def grad_alpha(self, obs, n_gates):
+        ox, pox = _u64(obs.x)
+        oz, poz = _u64(obs.z)
+        ow, pow_ = _f64(obs.w)
+        g = np.zeros(n_gates)
+        f = ctypes.c_double()
+        self.o._check(lib().oracle_adjoint(self.o._h, pox, poz, pow_, int(ow.shape[0]),
+                                           g.ctypes.data_as(_f64p), ctypes.byref(f)))
+        return f.value, g
 
 
 def commutes(W, px, pz, qx, qz) -> bool:

@@ -97,6 +97,8 @@ int pauli_product(int W, const Key& Q, const Key& P, Key* R) {
 
 enum Status { OK = 0, ERR_ARG = 1, ERR_CAPACITY = 3, ERR_TRACE_ZERO = 6, ERR_STATE = 8 };
 
+struct Frozen;
+
 struct Oracle {
     int n = 0, W = 0;
     std::vector<Key> Q;        // gates in Trotter order
@@ -169,6 +171,82 @@ int apply_gate(Oracle& o, int k) {
         o.support.push_back(std::move(s));
         o.gate_of_step.push_back(k);
     }
+    return OK;
+}
+
+
+// ---------------------------------------------------------------------------
+// Frozen-support forward and its adjoint (gradients with respect to the gate
+// coefficients).  The paper has no such step; this is the linear algebra of
+// Eq. (ITPP_PropRules) and the per-step normalisation with the kept support
+// of every step held fixed:
+//   raw_s[K] = a_K u_{s-1}[K] + [K commutes] s(Q,K) (-sinh) u_{s-1}[Q K],
+//              a_K = cosh(theta) if [K,Q] = 0 else 1, for K in S_s,
+//   u_s = raw_s / raw_s[I],   f = sum_j w_j u_L[P_j].
+// ---------------------------------------------------------------------------
+struct Frozen {
+    std::vector<int> gate;                          // gate index of step s (1-based steps)
+    std::vector<std::vector<Key>> support;          // S_s, s = 1..L
+};
+
+// One frozen step: u_prev on S_{s-1} -> raw on S_s.
+std::map<Key, double> frozen_step(int W, const std::map<Key, double>& u_prev, const Key& Q,
+                                  double ch, double msh, const std::vector<Key>& S) {
+    std::map<Key, double> raw;
+    for (const Key& K : S) raw[K] = 0.0;
+    for (const auto& [P, c] : u_prev) {
+        if (!commutes(W, P, Q)) {
+            auto it = raw.find(P);
+            if (it != raw.end()) it->second += c;
+        } else {
+            auto it = raw.find(P);
+            if (it != raw.end()) it->second += c * ch;
+            Key R;
+            int e = pauli_product(W, Q, P, &R);
+            auto jt = raw.find(R);
+            if (jt != raw.end()) jt->second += (c * msh) * (e == 0 ? 1.0 : -1.0);
+        }
+    }
+    return raw;
+}
+
+std::map<Key, double> normalise(const std::map<Key, double>& raw, double* D) {
+    Key I;
+    *D = raw.at(I);
+    const double inv = 1.0 / *D;
+    std::map<Key, double> u;
+    for (const auto& [K, v] : raw) u[K] = K.is_identity() ? 1.0 : v * inv;
+    return u;
+}
+
+double observe(const Oracle& o, const std::map<Key, double>& u, const uint64_t* ox,
+               const uint64_t* oz, const double* w, int m) {
+    double f = 0.0;
+    for (int j = 0; j < m; ++j) {
+        auto it = u.find(make_key(o.W, ox + (size_t)j * o.W, oz + (size_t)j * o.W));
+        if (it != u.end()) f += w[j] * it->second;
+    }
+    return f;
+}
+
+// Frozen forward over the recorded supports; keeps every state when asked.
+int frozen_forward(const Oracle& o, const double* alpha, std::vector<std::map<Key, double>>* states,
+                   std::vector<double>* Ds, std::map<Key, double>* last) {
+    std::map<Key, double> u;
+    u[Key{}] = 1.0;
+    if (states) states->push_back(u);
+    for (size_t s = 0; s < o.support.size(); ++s) {
+        const int k = o.gate_of_step[s];
+        const double theta = alpha[k] * o.dtau;
+        std::map<Key, double> raw = frozen_step(o.W, u, o.Q[k], std::cosh(theta),
+                                                -std::sinh(theta), o.support[s]);
+        double D = 0;
+        if (raw.find(Key{}) == raw.end()) return ERR_TRACE_ZERO;
+        u = normalise(raw, &D);
+        if (Ds) Ds->push_back(D);
+        if (states) states->push_back(u);
+    }
+    if (last) *last = u;
     return OK;
 }
 
@@ -263,6 +341,87 @@ double oracle_expect(void* h, const uint64_t* ox, const uint64_t* oz, const doub
         if (it != o.rho.end()) s += ow[j] * it->second;
     }
     return s;
+}
+
+// Run n_layers Trotter layers from the identity, recording the kept support
+// of every step (for the frozen-support forward and its adjoint).
+int oracle_record(void* h, int n_layers) {
+    Oracle& o = *static_cast<Oracle*>(h);
+    o.rho.clear();
+    o.rho[Key{}] = 1.0;
+    o.record = true;
+    o.support.clear();
+    o.gate_of_step.clear();
+    int st = oracle_apply_layers(h, n_layers);
+    o.record = false;
+    return st;
+}
+
+// f = sum_j w_j u_L[P_j] of the frozen forward with gate coefficients alpha
+// (n_gates values; the Hamiltonian's own when alpha is NULL).
+int oracle_frozen_value(void* h, const double* alpha, const uint64_t* ox, const uint64_t* oz,
+                        const double* w, int m, double* f) {
+    Oracle& o = *static_cast<Oracle*>(h);
+    std::map<Key, double> u;
+    int st = frozen_forward(o, alpha ? alpha : o.alpha.data(), nullptr, nullptr, &u);
+    if (st) return st;
+    *f = observe(o, u, ox, oz, w, m);
+    return OK;
+}
+
+// Gradient of the frozen f with respect to every gate coefficient alpha_k
+// (summed over the layers).  Reverse sweep: mu_s = df/du_s, then
+//   nu_s[K] = mu_s[K] / D_s (K != I),  nu_s[I] = -sum_{K != I} mu_s[K] u_s[K] / D_s,
+//   mu_{s-1}[P] = nu_s[P]                                  ({P,Q} = 0),
+//               = cosh nu_s[P] + s (-sinh) nu_s[Q P]      ([P,Q] = 0),
+//   df/dtheta_s = sum_{[P,Q]=0} u_{s-1}[P] (sinh nu_s[P] - s cosh nu_s[Q P]),
+// with nu_s = 0 outside S_s and theta_s = alpha_k dtau.
+int oracle_adjoint(void* h, const uint64_t* ox, const uint64_t* oz, const double* w, int m,
+                   double* grad_alpha, double* f) {
+    Oracle& o = *static_cast<Oracle*>(h);
+    std::vector<std::map<Key, double>> U;
+    std::vector<double> D;
+    int st = frozen_forward(o, o.alpha.data(), &U, &D, nullptr);
+    if (st) return st;
+    const size_t L = o.support.size();
+    *f = observe(o, U[L], ox, oz, w, m);
+    for (size_t k = 0; k < o.Q.size(); ++k) grad_alpha[k] = 0.0;
+    std::map<Key, double> mu;
+    for (const auto& kv : U[L]) mu[kv.first] = 0.0;
+    for (int j = 0; j < m; ++j) {
+        auto it = mu.find(make_key(o.W, ox + (size_t)j * o.W, oz + (size_t)j * o.W));
+        if (it != mu.end()) it->second += w[j];
+    }
+    for (size_t s = L; s >= 1; --s) {
+        const int k = o.gate_of_step[s - 1];
+        const Key& Q = o.Q[k];
+        const double theta = o.alpha[k] * o.dtau;
+        const double ch = std::cosh(theta), sh = std::sinh(theta), msh = -sh;
+        double dot = 0.0;
+        for (const auto& [K, v] : U[s])
+            if (!K.is_identity()) dot += mu[K] * v;
+        std::map<Key, double> nu;
+        for (const auto& [K, v] : mu) nu[K] = K.is_identity() ? -dot / D[s - 1] : v / D[s - 1];
+        auto nu_of = [&](const Key& K) {
+            auto it = nu.find(K);
+            return it == nu.end() ? 0.0 : it->second;
+        };
+        std::map<Key, double> mu_prev;
+        double g = 0.0;
+        for (const auto& [P, up] : U[s - 1]) {
+            if (!commutes(o.W, P, Q)) {
+                mu_prev[P] = nu_of(P);
+            } else {
+                Key R;
+                const double sg = pauli_product(o.W, Q, P, &R) == 0 ? 1.0 : -1.0;
+                mu_prev[P] = ch * nu_of(P) + sg * msh * nu_of(R);
+                g += up * (sh * nu_of(P) - sg * ch * nu_of(R));
+            }
+        }
+        grad_alpha[k] += g * o.dtau;
+        mu.swap(mu_prev);
+    }
+    return OK;
 }
 
 // Bit algebra exposed for the pin tests.

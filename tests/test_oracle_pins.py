@@ -337,3 +337,76 @@ def test_high_temperature_series():
     beta = 0.01
     series = -beta * float(np.sum(H.alpha ** 2))
     assert abs(o.expect(wl.energy_observable(H)) - series) < 5e-3 * abs(series)
+
+
+# ---------------------------------------------------------------------------
+# Adjoint of the frozen-support forward (gradients w.r.t. gate coefficients)
+# ---------------------------------------------------------------------------
+def _chain(n):
+    return wl.tfim_1d(n, np.linspace(0.9, 1.1, n - 1), np.linspace(0.8, 1.2, n))
+
+
+@pytest.mark.parametrize("obs_kind", ["zz", "energy"])
+def test_adjoint_matches_central_differences_of_frozen_forward(obs_kind):
+    H = _chain(6)
+    o = oracle.Oracle(H.n, H.gate_x, H.gate_z, H.alpha, 0.05, 1e-4)
+    fa = oracle.FrozenAdjoint(o, 6)
+    O = wl.zz_observables(6, [(2, 3)])[0] if obs_kind == "zz" else wl.energy_observable(H)
+    f, g = fa.grad_alpha(O, H.n_gates)
+    assert abs(f - fa.value(O)) < 1e-15 * max(1.0, abs(f))
+    eps = 1e-5
+    for k in range(H.n_gates):
+        a = H.alpha.copy(); a[k] += eps
+        fp = fa.value(O, a)
+        a = H.alpha.copy(); a[k] -= eps
+        fm = fa.value(O, a)
+        assert abs((fp - fm) / (2 * eps) - g[k]) <= 1e-7 * np.max(np.abs(g)) + 1e-12
+
+
+def test_adjoint_at_delta0_matches_dense_trotter_derivative():
+    H = _chain(4)
+    dtau, L = 0.1, 4
+    O = wl.zz_observables(4, [(1, 2)])[0]
+    o = oracle.Oracle(H.n, H.gate_x, H.gate_z, H.alpha, dtau, 0.0)
+    f, g = oracle.FrozenAdjoint(o, L).grad_alpha(O, H.n_gates)
+    Od = dense.pauli_dense(O.x[0], O.z[0], 4)
+
+    def dense_f(alpha):
+        H2 = wl.Hamiltonian(H.n, H.gate_x, H.gate_z, alpha)
+        rho = dense.trotter_rho(H2, dtau, L)
+        return float(np.real(np.trace(Od @ rho) / np.trace(rho)))
+
+    assert abs(dense_f(H.alpha) - f) < 1e-12
+    eps = 1e-5
+    for k in range(H.n_gates):
+        a = H.alpha.copy(); a[k] += eps
+        fp = dense_f(a)
+        a = H.alpha.copy(); a[k] -= eps
+        fm = dense_f(a)
+        assert abs((fp - fm) / (2 * eps) - g[k]) < 1e-7
+
+
+def test_energy_gradient_converges_to_exact_thermal_derivative():
+    # d<H>/dh_i = <dH/dh_i> - beta (<H dH/dh_i> - <H><dH/dh_i>) exactly, since
+    # H commutes with exp(-beta H); ITPP reaches it as dtau -> 0
+    n, beta = 5, 0.6
+    H = _chain(n)
+    i = 2                                   # field on site 2: alpha = -h_2
+    k = (n - 1) + i
+    E = wl.energy_observable(H)
+    Hd = dense.hamiltonian_dense(H)
+    w, U = np.linalg.eigh(Hd)
+    p = np.exp(-beta * (w - w.min())); p /= p.sum()
+    dH = -dense.pauli_dense(H.gate_x[k], H.gate_z[k], n)     # dH/dh_i = -X_i
+    ev = lambda A: float(np.real(np.sum(p * np.einsum("ji,jk,ki->i", U.conj(), A, U))))
+    exact = ev(dH) - beta * (ev(Hd @ dH) - ev(Hd) * ev(dH))
+    errs = []
+    for dtau in (0.1, 0.05, 0.025):
+        o = oracle.Oracle(H.n, H.gate_x, H.gate_z, H.alpha, dtau, 0.0)
+        fa = oracle.FrozenAdjoint(o, int(round(beta / dtau)))
+        f, g = fa.grad_alpha(E, H.n_gates)
+        # <H> = sum_j alpha_j c_j: explicit term d alpha_k/dh_i = -1 times c_k
+        c_k = o.coeffs(H.gate_x[k:k + 1], H.gate_z[k:k + 1])[0]
+        total = -c_k + (-1.0) * g[k]
+        errs.append(abs(total - exact))
+    assert errs[1] < errs[0] and errs[2] < errs[1] and errs[2] < 1e-3, errs
