@@ -56,6 +56,13 @@ def parse():
                     help="untimed layers before warm-up (-1: until the bound is reached)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--mode", default="headline", choices=["headline", "batch", "adjoint"],
+                    help="headline: the metric line; batch / adjoint: the extension "
+                         "timings against plain single-instance runs")
+    ap.add_argument("--batch-cap-log2", type=int, default=16)
+    ap.add_argument("--adjoint-layers", type=int, default=50)
+    ap.add_argument("--adjoint-ckpt", type=int, default=10)
+    ap.add_argument("--batch-layers", type=int, default=5)
     ap.add_argument("--ref-gates", type=int, default=224,
                     help="oracle gates per reference step (bounded CPU sample)")
     return ap.parse_args()
@@ -211,8 +218,146 @@ def run_reference(args, w):
 # ---------------------------------------------------------------------------
 # GPU arm
 # ---------------------------------------------------------------------------
+def run_batch(args):
+    """64 independent open chains (n ~ U{16..64}, h ~ U[0.5, 2], J = 1,
+    dtau = 0.02, delta = 1e-7, at most 2^k terms each, top-M): the first
+    layers from the identity, batched (one graph launch per layer) against
+    the same 64 propagations run one after another as plain runs."""
+    import torch
+    import paper_2601_14400_gb300 as itpp
+    if not os.path.exists(itpp.LIB_PATH):
+        itpp.build()
+    ns, hs = wl.batch_field_sweep()
+    hams = [wl.tfim_1d(n, 1.0, h) for n, h in zip(ns, hs)]
+    dtau, delta, M, L = 0.02, 1e-7, 1 << args.batch_cap_log2, args.batch_layers
+    stream = torch.cuda.Stream()
+    # batched
+    bp = itpp.BatchPropagator(hams, dtau, delta, M, cap_policy=1, stream=stream)
+    bp.apply_trotter_layer(0)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    bp.apply_trotter_layer(L)
+    e1.record(stream)
+    bp.synchronize()
+    t_batch = e0.elapsed_time(e1)
+    terms_b = sum(bp.stats(b)["terms_in"] for b in range(len(hams)))
+    counts_b, _ = bp.counts()
+    energy_b = [bp.expect(b, wl.energy_observable(H)) for b, H in enumerate(hams[:4])]
+    bp.close()
+    # plain, one instance after another
+    t_plain, terms_p, counts_p, energy_p = 0.0, 0, [], []
+    for b, H in enumerate(hams):
+        g = itpp.Propagator(H.n, H.gate_x, H.gate_z, H.alpha, dtau, delta, M, 1, stream=stream)
+        g.synchronize()
+        e0.record(stream)
+        g.apply_trotter_layer(L)
+        e1.record(stream)
+        g.synchronize()
+        t_plain += e0.elapsed_time(e1)
+        terms_p += g.stats()["terms_in"]
+        counts_p.append(g.count())
+        if b < 4:
+            energy_p.append(g.expect(wl.energy_observable(H)))
+        g.close()
+    same = (list(map(int, counts_b)) == counts_p) and energy_b == energy_p
+    line = {"metric": "batched vs plain: Pauli terms/s per Trotter gate", "mode": "batch",
+            "value": terms_b / (t_batch * 1e-3), "unit": UNIT,
+            "plain_value": terms_p / (t_plain * 1e-3), "speedup": t_plain / t_batch,
+            "batched_ms": t_batch, "plain_ms": t_plain, "identical_results": bool(same),
+            "config": {"workload": "field sweep: 64 open TFIM chains, n~U{16..64}, "
+                                   "h~U[0.5,2], J=1", "dtau": dtau, "delta": delta,
+                       "cap_M": M, "cap_policy": "top-M", "layers": L,
+                       "terms_final": int(sum(counts_b))},
+            "dtype": "f64", "data": "synthetic"}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def run_adjoint(args):
+    """n = 32 open chain with per-site fields and couplings (63 parameters),
+    dtau = 0.02, 50 layers, |c| <= 1e-7 dropped: the energy and <Z15 Z16>
+    gradients by the adjoint sweep (frozen support, snapshots every 10
+    layers), timed against the plain forward of the same propagation."""
+    import torch
+    import paper_2601_14400_gb300 as itpp
+    if not os.path.exists(itpp.LIB_PATH):
+        itpp.build()
+    w = wl.WORKLOADS["adjoint_n32"]
+    H = w.H
+    L = args.adjoint_layers
+    g = itpp.Propagator.from_workload(w)
+    E = w.observables["energy"]
+    ZZ = w.observables["Z15Z16"]
+    free0 = torch.cuda.mem_get_info()[0]
+    # plain forward
+    g.reset()
+    g.synchronize()
+    t0 = time.perf_counter()
+    g.apply_trotter_layer(L)
+    c_fwd = g.coeffs(H.gate_x, H.gate_z)
+    t_fwd = time.perf_counter() - t0
+    count = g.count()
+    st = g.stats()
+    # adjoint (its own forward, snapshots, recomputation, reverse sweep)
+    peak = [0]
+    stop = [False]
+
+    def poll():
+        while not stop[0]:
+            peak[0] = max(peak[0], free0 - torch.cuda.mem_get_info()[0])
+            time.sleep(0.02)
+    th = threading.Thread(target=poll, daemon=True)
+    th.start()
+    ck = args.adjoint_ckpt
+    t0 = time.perf_counter()
+    fE, gE = g.adjoint(L, E, ckpt_every=ck)
+    t_adjE = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    fZ, gZ = g.adjoint(L, ZZ, ckpt_every=ck)
+    t_adjZ = time.perf_counter() - t0
+    stop[0] = True
+    th.join()
+    # d<H>/dp: explicit term c_k plus the adjoint, d alpha_k / dp = -1
+    dE = -(c_fwd + gE)
+    dZ = -gZ
+    # loose check against central differences of the (unfrozen) forward
+    eps = 1e-5
+    fd = {}
+    for k in (0, H.n_gates - 1):
+        vals = []
+        for sgn in (1, -1):
+            a = H.alpha.copy()
+            a[k] += sgn * eps
+            g.set_alpha(a)
+            g.reset()
+            g.apply_trotter_layer(L)
+            vals.append(float(np.dot(a, g.coeffs(H.gate_x, H.gate_z))))
+        fd[k] = -(vals[0] - vals[1]) / (2 * eps)
+    g.set_alpha(H.alpha)
+    line = {"metric": "adjoint vs plain forward: wall-time ratio", "mode": "adjoint",
+            "value": t_adjE / t_fwd, "unit": "x forward", "forward_s": t_fwd,
+            "adjoint_energy_s": t_adjE, "adjoint_zz_s": t_adjZ,
+            "peak_device_bytes_approx": int(peak[0]), "terms_final": count,
+            "terms_in_forward": st["terms_in"],
+            "energy": fE, "zz_15_16": fZ,
+            "dE_dJ0": float(dE[0]), "dE_dh31": float(dE[-1]),
+            "fd_dE_dJ0": fd[0], "fd_dE_dh31": fd[H.n_gates - 1],
+            "grad_norm_energy": float(np.linalg.norm(dE)),
+            "grad_norm_zz": float(np.linalg.norm(dZ)),
+            "config": {"workload": w.name, "layers": L, "ckpt_every": ck,
+                       "delta": w.delta, "dtau": w.dtau, "params": H.n_gates},
+            "dtype": "f64", "data": "synthetic"}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def main():
     args = parse()
+    if args.mode == "batch":
+        return run_batch(args)
+    if args.mode == "adjoint":
+        return run_adjoint(args)
     w = wl.WORKLOADS[args.workload]
     if args.cap_log2:
         w.cap_M = 1 << args.cap_log2

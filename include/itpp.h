@@ -148,6 +148,11 @@ itpp_status itpp_apply_trotter_layer(itpp_handle h, int n_layers);
  * elementary step as inside itpp_apply_trotter_layer.  Asynchronous. */
 itpp_status itpp_apply_gate(itpp_handle h, int k);
 
+/* Reset the state to the identity operator (Algorithm 1, "Initialize
+ * rho = I") and clear the statistics and a stored device error.
+ * Asynchronous. */
+itpp_status itpp_reset(itpp_handle h);
+
 /* Threshold truncation of the current (normalised) state: keep |c| > delta,
  * then renormalise (Sec. II.B "Coefficient threshold"; Algorithm 1
  * "Truncate and normalize").  delta >= 0; a delta >= 1 would drop the
@@ -210,6 +215,80 @@ itpp_status itpp_get_stats(itpp_handle h, itpp_stats* out);
  * device time in milliseconds. */
 itpp_status itpp_profile_enable(itpp_handle h, int enable);
 itpp_status itpp_profile_read(itpp_handle h, int kid, uint64_t* launches, double* total_ms);
+
+/* ---------------------------------------------------------------------------
+ * Gradients (adjoint of the frozen-support propagation)
+ * ------------------------------------------------------------------------- */
+
+/* Replace the gate coefficients alpha_k (n_gates values, host) of a handle;
+ * the host recomputes the per-gate weights.  The state is unchanged. */
+itpp_status itpp_set_alpha(itpp_handle h, const double* alpha);
+
+/* Gradient of f = sum_j w_j c_{P_j}(beta) with respect to every gate
+ * coefficient alpha_k, where c is the normalised state after n_layers Trotter
+ * layers from the identity and the kept support of every elementary step is
+ * held at what the forward produced ("frozen support").  The paper has no
+ * such step; it is the linear algebra of Eq. (ITPP_PropRules) and the
+ * per-step trace normalisation (Sec. II.C), evaluated by a reverse sweep.
+ * The call resets the handle to the identity, runs the forward (saving a
+ * snapshot every ckpt_every layers), then for each segment from the last
+ * recomputes its steps from the snapshot and sweeps them backwards.
+ *   obs_x/z, w   host, m observable strings and weights (w_j = df/dc_{P_j}).
+ *   grad_alpha   host, n_gates: df/dalpha_k summed over the layers.
+ *   value        host or NULL: f.
+ * Requires cap_policy 0 (threshold truncation only).  Device memory: one
+ * snapshot per segment plus the states and three int32 maps of every step
+ * of the largest segment, allocated for the call.  After the call the handle
+ * holds the forward's final state.  Synchronising. */
+itpp_status itpp_adjoint(itpp_handle h, int n_layers, int ckpt_every, const uint64_t* obs_x,
+                         const uint64_t* obs_z, const double* w, int m, double* grad_alpha,
+                         double* value);
+
+/* ---------------------------------------------------------------------------
+ * Batched propagation: many independent instances in shared launches
+ * ------------------------------------------------------------------------- */
+
+/* Create B independent propagations (Algorithm 1 for each), advanced
+ * together: in every Trotter layer, gate g of every instance that has one
+ * runs in the same kernel launches, and the whole layer is one CUDA graph
+ * launch.  Each instance's state is bit-identical to a plain run of the same
+ * Hamiltonian with the same parameters.
+ *   B            1..65535 instances.
+ *   n[B]         sites per instance (1..128); all instances use
+ *                W = ceil(max n / 64) mask words.
+ *   n_gates[B]   gates per layer per instance (instances with fewer gates sit
+ *                out the later steps of a layer).
+ *   gate_x/z     host, concatenated over instances in order (instance b's
+ *                gates follow instance b-1's), W words per gate.
+ *   alpha        host, concatenated likewise.
+ *   dtau, p      as in itpp_create; cap_M bounds every instance separately.
+ *   cuda_stream  stream to run on; NULL makes the library create its own
+ *                (graph capture needs a non-legacy stream).
+ * Memory: per instance two buffers of 2*cap_M terms, a table and a control
+ * block (about 0.6 MB).  Errors: as itpp_create. */
+itpp_status itpp_batch_create(int B, const int* n, const int* n_gates, const uint64_t* gate_x,
+                              const uint64_t* gate_z, const double* alpha, double dtau,
+                              const itpp_params* p, void* cuda_stream, itpp_batch_handle* out);
+itpp_status itpp_batch_destroy(itpp_batch_handle h);
+
+/* n_layers Trotter layers for every instance.  Asynchronous.  An instance
+ * that meets a device error (bound, probe limit) stops; the others go on. */
+itpp_status itpp_batch_apply_trotter_layer(itpp_batch_handle h, int n_layers);
+
+/* Wait; ITPP_OK if every instance is healthy, else the first error. */
+itpp_status itpp_batch_synchronize(itpp_batch_handle h);
+
+/* Term count (and, when statuses != NULL, the status) of every instance;
+ * host arrays of B entries.  Synchronising. */
+itpp_status itpp_batch_get_counts(itpp_batch_handle h, uint64_t* counts, int* statuses);
+
+/* Instance b: statistics, normalised terms (as itpp_get_terms) and an
+ * expectation value (as itpp_expect).  Synchronising. */
+itpp_status itpp_batch_get_stats(itpp_batch_handle h, int b, itpp_stats* out);
+itpp_status itpp_batch_get_terms(itpp_batch_handle h, int b, uint64_t* x, uint64_t* z,
+                                 double* c, uint64_t capacity, uint64_t* count);
+itpp_status itpp_batch_expect(itpp_batch_handle h, int b, const uint64_t* obs_x,
+                              const uint64_t* obs_z, const double* obs_w, int m, double* out);
 
 /* ---------------------------------------------------------------------------
  * One gate without device allocation

@@ -70,6 +70,22 @@ _SIGNATURES = [
     ("itpp_get_stats", ctypes.c_int, [_vp, ctypes.POINTER(itpp_stats)]),
     ("itpp_profile_enable", ctypes.c_int, [_vp, ctypes.c_int]),
     ("itpp_profile_read", ctypes.c_int, [_vp, ctypes.c_int, _u64p, _f64p]),
+    ("itpp_set_alpha", ctypes.c_int, [_vp, _f64p]),
+    ("itpp_reset", ctypes.c_int, [_vp]),
+    ("itpp_adjoint", ctypes.c_int, [_vp, ctypes.c_int, ctypes.c_int, _u64p, _u64p, _f64p,
+                                    ctypes.c_int, _f64p, _f64p]),
+    ("itpp_batch_create", ctypes.c_int, [ctypes.c_int, _i32p, _i32p, _u64p, _u64p, _f64p,
+                                         ctypes.c_double, ctypes.POINTER(itpp_params), _vp,
+                                         ctypes.POINTER(_vp)]),
+    ("itpp_batch_destroy", ctypes.c_int, [_vp]),
+    ("itpp_batch_apply_trotter_layer", ctypes.c_int, [_vp, ctypes.c_int]),
+    ("itpp_batch_synchronize", ctypes.c_int, [_vp]),
+    ("itpp_batch_get_counts", ctypes.c_int, [_vp, _u64p, _i32p]),
+    ("itpp_batch_get_stats", ctypes.c_int, [_vp, ctypes.c_int, ctypes.POINTER(itpp_stats)]),
+    ("itpp_batch_get_terms", ctypes.c_int, [_vp, ctypes.c_int, _u64p, _u64p, _f64p,
+                                            ctypes.c_uint64, _u64p]),
+    ("itpp_batch_expect", ctypes.c_int, [_vp, ctypes.c_int, _u64p, _u64p, _f64p, ctypes.c_int,
+                                         _f64p]),
     ("itpp_gate_apply_noalloc", ctypes.c_int, [ctypes.c_int, _u64p, _u64p, ctypes.c_double,
                                                ctypes.c_double, ctypes.c_double, _vp, _vp,
                                                ctypes.c_uint64, _vp, _vp, ctypes.c_uint64, _vp,
@@ -257,6 +273,26 @@ class Propagator:
         _check(lib().itpp_get_stats(self._h, ctypes.byref(s)), "itpp_get_stats")
         return {k: int(getattr(s, k)) for k, _ in itpp_stats._fields_}
 
+    def reset(self):
+        _check(lib().itpp_reset(self._h), "itpp_reset")
+
+    def set_alpha(self, alpha):
+        al, pal = _f64(alpha)
+        _check(lib().itpp_set_alpha(self._h, pal), "itpp_set_alpha")
+
+    def adjoint(self, n_layers, obs, ckpt_every=10):
+        """(f, df/dalpha) for f = sum_j w_j c_{P_j} after n_layers layers
+        from the identity, support frozen; see include/itpp.h."""
+        ox, pox = _u64(obs.x)
+        oz, poz = _u64(obs.z)
+        ow, pow_ = _f64(obs.w)
+        g = np.zeros(self.n_gates)
+        f = ctypes.c_double()
+        _check(lib().itpp_adjoint(self._h, int(n_layers), int(ckpt_every), pox, poz, pow_,
+                                  int(ow.shape[0]), g.ctypes.data_as(_f64p), ctypes.byref(f)),
+               "itpp_adjoint")
+        return f.value, g
+
     def profile_enable(self, on=True):
         _check(lib().itpp_profile_enable(self._h, 1 if on else 0), "itpp_profile_enable")
 
@@ -266,3 +302,91 @@ class Propagator:
         _check(lib().itpp_profile_read(self._h, int(kid), ctypes.byref(n), ctypes.byref(ms)),
                "itpp_profile_read")
         return int(n.value), float(ms.value)
+
+
+class BatchPropagator:
+    """B independent ITPP propagations advanced in shared launches."""
+
+    def __init__(self, hams, dtau, delta, cap_M, cap_policy=0, stream=None, table_load_pct=0):
+        self.B = len(hams)
+        self.ns = [int(H.n) for H in hams]
+        self.W = (max(self.ns) + 63) // 64
+        W = self.W
+        gx = np.concatenate([_pad_words(H.gate_x, W) for H in hams])
+        gz = np.concatenate([_pad_words(H.gate_z, W) for H in hams])
+        al = np.concatenate([np.asarray(H.alpha, dtype=np.float64) for H in hams])
+        n = np.asarray(self.ns, dtype=np.int32)
+        ng = np.asarray([H.n_gates for H in hams], dtype=np.int32)
+        gx, pgx = _u64(gx)
+        gz, pgz = _u64(gz)
+        al, pal = _f64(al)
+        p = itpp_params()
+        p.delta = float(delta)
+        p.cap_M = int(cap_M)
+        p.cap_policy = int(cap_policy)
+        p.table_load_pct = int(table_load_pct)
+        h = _vp()
+        st = lib().itpp_batch_create(self.B, n.ctypes.data_as(_i32p), ng.ctypes.data_as(_i32p),
+                                     pgx, pgz, pal, float(dtau), ctypes.byref(p),
+                                     _stream_ptr(stream), ctypes.byref(h))
+        _check(st, "itpp_batch_create")
+        self._h = h
+
+    def close(self):
+        if getattr(self, "_h", None):
+            lib().itpp_batch_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def apply_trotter_layer(self, n_layers=1):
+        _check(lib().itpp_batch_apply_trotter_layer(self._h, int(n_layers)),
+               "itpp_batch_apply_trotter_layer")
+
+    def synchronize(self):
+        _check(lib().itpp_batch_synchronize(self._h), "itpp_batch_synchronize")
+
+    def counts(self):
+        c = np.zeros(self.B, dtype=np.uint64)
+        s = np.zeros(self.B, dtype=np.int32)
+        lib().itpp_batch_get_counts(self._h, c.ctypes.data_as(_u64p), s.ctypes.data_as(_i32p))
+        return c.astype(np.int64), s
+
+    def stats(self, b):
+        s = itpp_stats()
+        _check(lib().itpp_batch_get_stats(self._h, int(b), ctypes.byref(s)), "itpp_batch_get_stats")
+        return {k: int(getattr(s, k)) for k, _ in itpp_stats._fields_}
+
+    def terms(self, b):
+        got = ctypes.c_uint64()
+        c_all, _ = self.counts()
+        n = int(c_all[b])
+        x = np.zeros((n, self.W), dtype=np.uint64)
+        z = np.zeros((n, self.W), dtype=np.uint64)
+        c = np.zeros(n)
+        _check(lib().itpp_batch_get_terms(self._h, int(b), x.ctypes.data_as(_u64p),
+                                          z.ctypes.data_as(_u64p), c.ctypes.data_as(_f64p), n,
+                                          ctypes.byref(got)), "itpp_batch_get_terms")
+        return x, z, c
+
+    def expect(self, b, obs):
+        ox, pox = _u64(_pad_words(obs.x, self.W))
+        oz, poz = _u64(_pad_words(obs.z, self.W))
+        ow, pow_ = _f64(obs.w)
+        out = ctypes.c_double()
+        _check(lib().itpp_batch_expect(self._h, int(b), pox, poz, pow_, int(ow.shape[0]),
+                                       ctypes.byref(out)), "itpp_batch_expect")
+        return float(out.value)
+
+
+def _pad_words(a, W):
+    a = np.asarray(a, dtype=np.uint64)
+    if a.shape[1] == W:
+        return a
+    out = np.zeros((a.shape[0], W), dtype=np.uint64)
+    out[:, :a.shape[1]] = a
+    return out

@@ -1,0 +1,529 @@
+// itpp_adjoint.cu -- gradients of a propagated expectation value with respect
+// to every gate coefficient alpha_k, by a reverse sweep over the steps with
+// the kept support of every step frozen (the paper has no such step; this is
+// the linear algebra of Eq. (ITPP_PropRules) and the per-step normalisation).
+//
+// With u_s the normalised state after step s (support S_s), D_s its identity
+// coefficient before normalisation and f = sum_j w_j u_L[P_j]:
+//   nu_s[K] = mu_s[K] / D_s (K != I),  nu_s[I] = -sum_{K != I} mu_s[K] u_s[K] / D_s
+//   mu_{s-1}[P] = nu_s[P]                                ({P,Q} = 0)
+//               = cosh nu_s[P] + s (-sinh) nu_s[Q P]    ([P,Q] = 0)
+//   df/dtheta_s = sum_{[P,Q]=0} u_{s-1}[P] (sinh nu_s[P] - s cosh nu_s[Q P])
+// where mu_s = df/du_s, nu_s = 0 outside S_s and theta_s = alpha_k dtau.
+//
+// Memory: the forward saves a snapshot every ckpt_every layers; each segment
+// is recomputed from its snapshot into an arena that keeps every step's state
+// and, per input term, the output positions of its children (itself, a new
+// partner string, or the partner that was present).  The reverse sweep then
+// gathers through those positions -- no atomics, fixed-order reductions.
+// Output order inside a recomputed segment need not match the first forward,
+// so the adjoint vector is carried across a segment boundary by key (a
+// table lookup into the snapshot's keys).
+#include <cmath>
+#include <cstring>
+#include <vector>
+
+#include "itpp.h"
+#include "itpp_common.cuh"
+#include "itpp_ctx.h"
+#include "itpp_gate_body.cuh"
+#include "itpp_launch.h"
+
+using namespace itpp;
+
+namespace {
+
+constexpr int kRB = 256;      // reduction block
+constexpr int kRGrid = 512;   // fixed reduction grid: deterministic partial order
+
+template <int W>
+GateArg<W> gate_arg_of(const HostGate& h) {
+    GateArg<W> g;
+    for (int w = 0; w < W; ++w) { g.qx[w] = h.qx[w]; g.qz[w] = h.qz[w]; }
+    g.ch = h.ch;
+    g.msh = h.msh;
+    g.qyy = h.qyy;
+    return g;
+}
+
+__device__ __forceinline__ double block_sum(double v, double* s) {
+    s[threadIdx.x] = v;
+    __syncthreads();
+    for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+        if ((int)threadIdx.x < o) s[threadIdx.x] = __dadd_rn(s[threadIdx.x], s[threadIdx.x + o]);
+        __syncthreads();
+    }
+    const double r = s[0];
+    __syncthreads();
+    return r;
+}
+
+__global__ void k_adj_log(const DevCtl* ctl, unsigned long long* log, int s) {
+    if (threadIdx.x == 0) log[s] = ctl->status ? ~0ULL : ctl->count[ctl->cur];
+}
+
+// Snapshot of the current state: AoS keys and normalised coefficients.
+template <int W>
+__global__ void __launch_bounds__(256)
+k_adj_snapshot(const PKey<W>* k0, const double* c0, const PKey<W>* k1, const double* c1,
+               const DevCtl* ctl, PKey<W>* keys, double* coef) {
+    const int cur = ctl->cur;
+    const uint64_t n = live_count(ctl, cur);
+    const double rn = ctl->rnorm[cur];
+    const PKey<W>* ks = cur ? k1 : k0;
+    const double* cs = cur ? c1 : c0;
+    for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+         i += (uint64_t)gridDim.x * blockDim.x) {
+        const PKey<W> K = ks[i];
+        keys[i] = K;
+        coef[i] = normalised(cs[i], rn, key_is_zero(K));
+    }
+}
+
+// Before recomputing step r: input region r-1 holds cnt[r-1] terms scaled by
+// rn[r-1]; outputs go to region r.
+__global__ void k_adj_prep(DevCtl* ctl, const unsigned long long* cnt, const double* rn, int r,
+                           unsigned long long cap) {
+    if (threadIdx.x != 0) return;
+    ctl->cur = 0;
+    ctl->count[0] = cnt[r - 1];
+    ctl->count[1] = 0;
+    ctl->rnorm[0] = rn[r - 1];
+    ctl->norm[0] = 1.0;
+    ctl->buf_cap = cap;
+    ctl->sel_active = 0;
+}
+
+template <int W>
+__global__ void __launch_bounds__(256)
+k_adj_insert(const PKey<W>* kin, const double* cin, DevCtl* ctl, Slot<W>* table,
+             uint64_t alloc_slots, GateArg<W> g, int probe_limit) {
+    if (ctl->status) return;
+    const uint64_t n = live_count(ctl, 0);
+    const uint64_t mask = table_mask(n, alloc_slots, 50);
+    const unsigned gen = ctl->gen;
+    int probes = 0;
+    for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+         i += (uint64_t)gridDim.x * blockDim.x)
+        insert_one(kin, cin, i, ctl, table, mask, gen, g, probe_limit, &probes);
+}
+
+template <int W>
+__global__ void __launch_bounds__(256)
+k_adj_main(const PKey<W>* kin, const double* cin, PKey<W>* kout, double* cout, DevCtl* ctl,
+           const Slot<W>* table, uint64_t alloc_slots, GateArg<W> g, double delta,
+           uint64_t cap_out, int probe_limit, StepMaps maps) {
+    __shared__ uint32_t s_scan[256 / 32];
+    __shared__ unsigned long long s_base;
+    if (ctl->status) return;
+    const uint64_t n = live_count(ctl, 0);
+    const double rnorm = ctl->rnorm[0];
+    const unsigned long long dbits = (unsigned long long)__double_as_longlong(delta);
+    const unsigned gen = ctl->gen;
+    const uint64_t mask = table_mask(n, alloc_slots, 50);
+    const uint64_t tiles = (n + 511) / 512;
+    int probes = 0;
+    for (uint64_t t = blockIdx.x; t < tiles; t += gridDim.x)
+        gate_tile<W, 256, 2, true>(t, n, kin, cin, kout, cout, ctl, 0, table, mask, gen, g, rnorm,
+                                   dbits, cap_out, probe_limit, s_scan, &s_base, &probes, maps);
+}
+
+__global__ void k_adj_post(DevCtl* ctl, uint64_t cap_M, unsigned long long* cnt, double* rn,
+                           int r) {
+    if (threadIdx.x != 0 || ctl->status) return;
+    post_one(ctl, cap_M, 0);
+    cnt[r] = ctl->count[1];
+    rn[r] = ctl->rnorm[1];
+}
+
+// Seed: mu[i] = sum of the weights of the observable strings equal to key i.
+template <int W>
+__global__ void __launch_bounds__(256)
+k_adj_seed(const PKey<W>* keys, uint64_t n, const uint64_t* ox, const uint64_t* oz,
+           const double* wsum, const int* tab, int tsize, double* mu) {
+    const uint64_t mask = (uint64_t)tsize - 1;
+    for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+         i += (uint64_t)gridDim.x * blockDim.x) {
+        const PKey<W> K = keys[i];
+        double v = 0.0;
+        uint64_t h = key_hash(K) & mask;
+        for (int p = 0; p < tsize; ++p) {
+            const int e = tab[h];
+            if (e < 0) break;
+            PKey<W> o;
+            for (int w = 0; w < W; ++w) { o.x[w] = ox[(size_t)e * W + w]; o.z[w] = oz[(size_t)e * W + w]; }
+            if (key_eq(o, K)) { v = wsum[e]; break; }
+            h = (h + 1) & mask;
+        }
+        mu[i] = v;
+    }
+}
+
+// Per distinct observable string (first occurrence), the sum of its weights.
+__global__ void k_adj_wsum(const int* first, const double* w, int m, double* wsum) {
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    for (int j = 0; j < m; ++j) wsum[j] = 0.0;
+    for (int j = 0; j < m; ++j) wsum[first[j]] = __dadd_rn(wsum[first[j]], w[j]);
+}
+
+// dot = sum_{j != idpos} mu[j] u[j], u = raw * rn; block partials.
+__global__ void __launch_bounds__(kRB)
+k_adj_dot(const double* raw, const double* mu, uint64_t n, const unsigned long long* idpos,
+          const double* rn, double* partials) {
+    __shared__ double s[kRB];
+    const unsigned long long id = *idpos;
+    const double r = *rn;
+    double acc = 0.0;
+    for (uint64_t j = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; j < n;
+         j += (uint64_t)gridDim.x * blockDim.x)
+        if (j != id) acc = __dadd_rn(acc, __dmul_rn(mu[j], __dmul_rn(raw[j], r)));
+    const double b = block_sum(acc, s);
+    if (threadIdx.x == 0) partials[blockIdx.x] = b;
+}
+
+// nu_I = -dot / D = -dot * rn (one block).
+__global__ void __launch_bounds__(kRB)
+k_adj_dot_final(const double* partials, int np, const double* rn, double* nu_i) {
+    __shared__ double s[kRB];
+    double acc = 0.0;
+    for (int i = threadIdx.x; i < np; i += blockDim.x) acc = __dadd_rn(acc, partials[i]);
+    const double b = block_sum(acc, s);
+    if (threadIdx.x == 0) *nu_i = -__dmul_rn(b, *rn);
+}
+
+// mu_{s-1} from nu_s through the recorded output positions; partial sums of
+// df/dtheta_s.
+template <int W>
+__global__ void __launch_bounds__(kRB)
+k_adj_back(const PKey<W>* kin, const double* cin, uint64_t n_in, const double* rn_in,
+           const int* self_out, const int* emit_out, const int* part_src, const double* mu_out,
+           const unsigned long long* idpos_out, const double* rn_out, const double* nu_i,
+           GateArg<W> g, double sh, double chd, double* mu_in, double* partials) {
+    __shared__ double s[kRB];
+    const double ri = *rn_in, ro = *rn_out, nI = *nu_i;
+    const long long id = (long long)*idpos_out;
+    double acc = 0.0;
+    for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n_in;
+         i += (uint64_t)gridDim.x * blockDim.x) {
+        const PKey<W> K = kin[i];
+        const int so = self_out[i];
+        const double vs = so < 0 ? 0.0 : (so == id ? nI : __dmul_rn(mu_out[so], ro));
+        if (!commutes(K, g)) {
+            mu_in[i] = vs;
+        } else {
+            const double sg = product_negative(K, g) ? -1.0 : 1.0;
+            int po = emit_out[i];
+            if (po < 0 && part_src[i] >= 0) po = self_out[part_src[i]];
+            const double vp = po < 0 ? 0.0 : (po == id ? nI : __dmul_rn(mu_out[po], ro));
+            mu_in[i] = __dadd_rn(__dmul_rn(g.ch, vs), __dmul_rn(sg * g.msh, vp));
+            const double u = normalised(cin[i], ri, key_is_zero(K));
+            acc = __dadd_rn(acc, __dmul_rn(u, __dsub_rn(__dmul_rn(sh, vs),
+                                                        __dmul_rn(sg * chd, vp))));
+        }
+    }
+    const double b = block_sum(acc, s);
+    if (threadIdx.x == 0) partials[blockIdx.x] = b;
+}
+
+__global__ void __launch_bounds__(kRB)
+k_adj_gsum(const double* partials, int np, double* gstep, long long s) {
+    __shared__ double sh[kRB];
+    double acc = 0.0;
+    for (int i = threadIdx.x; i < np; i += blockDim.x) acc = __dadd_rn(acc, partials[i]);
+    const double b = block_sum(acc, sh);
+    if (threadIdx.x == 0) gstep[s] = b;
+}
+
+template <int W>
+__global__ void __launch_bounds__(256)
+k_adj_remap_insert(const PKey<W>* keys, const double* mu, uint64_t n, Slot<W>* table,
+                   uint64_t alloc_slots, DevCtl* ctl, int probe_limit) {
+    const uint64_t mask = table_mask(n, alloc_slots, 50);
+    const unsigned gen = ctl->gen;
+    int probes = 0;
+    for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+         i += (uint64_t)gridDim.x * blockDim.x)
+        if (!table_insert(table, mask, gen, keys[i], mu[i], (uint32_t)i, probe_limit, &probes))
+            set_status(ctl, ST_HASH_PROBE, 30);
+}
+
+template <int W>
+__global__ void __launch_bounds__(256)
+k_adj_remap_lookup(const PKey<W>* keys, uint64_t n, uint64_t n_table, double* mu,
+                   const Slot<W>* table, uint64_t alloc_slots, DevCtl* ctl, int probe_limit) {
+    const uint64_t mask = table_mask(n_table, alloc_slots, 50);
+    const unsigned gen = ctl->gen;
+    int probes = 0;
+    for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+         i += (uint64_t)gridDim.x * blockDim.x) {
+        double v = 0.0;
+        if (!table_find(table, mask, gen, keys[i], &v, probe_limit, ctl, &probes))
+            set_status(ctl, ST_STATE, 31);   // the sets at a boundary must agree
+        mu[i] = v;
+    }
+}
+
+__global__ void k_adj_bump_gen(DevCtl* ctl) {
+    if (threadIdx.x == 0) ctl->gen = ctl->gen + 1u;
+}
+
+// The adjoint shares the handle's merge table: its generations continue the
+// handle's, and the handle continues after the adjoint's, so no stale slot
+// ever reads as occupied.
+__global__ void k_adj_gen_copy(DevCtl* dst, const DevCtl* src) {
+    if (threadIdx.x == 0) dst->gen = src->gen + 1u;
+}
+
+// grad_alpha[k] = dtau * sum over layers of df/dtheta at gate k.
+__global__ void k_adj_params(const double* gstep, int n_layers, int n_gates, double dtau,
+                             double* grad) {
+    for (int k = threadIdx.x; k < n_gates; k += blockDim.x) {
+        double acc = 0.0;
+        for (int l = 0; l < n_layers; ++l)
+            acc = __dadd_rn(acc, gstep[(size_t)l * n_gates + k]);
+        grad[k] = __dmul_rn(acc, dtau);
+    }
+}
+
+struct DevBuf {
+    void* p = nullptr;
+    ~DevBuf() { if (p) cudaFree(p); }
+    bool alloc(size_t bytes) { return cudaMalloc(&p, bytes ? bytes : 16) == cudaSuccess; }
+    template <class T> T* as() const { return static_cast<T*>(p); }
+};
+
+template <int W>
+itpp_status adjoint_w(itpp_ctx* h, int L, int K, const uint64_t* obs_x, const uint64_t* obs_z,
+                      const double* seed, int m, double* grad_alpha, double* value) {
+    DeviceState& s = h->s;
+    cudaStream_t st = h->stream;
+    const int G = (int)h->gates.size();
+    const long long S = (long long)L * G;
+    const int n_seg = (L + K - 1) / K;
+    const size_t kb = sizeof(PKey<W>);
+    const int grid = s.num_sms * 8;
+    auto chk = [&](cudaError_t e) { return e == cudaSuccess; };
+
+    // ---- forward from the identity, logging counts, snapshot per segment
+    DevBuf log;
+    if (!log.alloc((size_t)(S + 1) * 8)) return ITPP_ERR_ALLOC;
+    if (!chk(launch_reset_identity(s, st))) return ITPP_ERR_CUDA;
+    std::vector<DevBuf> snap((size_t)n_seg);
+    std::vector<uint64_t> snap_n((size_t)n_seg);
+    for (int j = 0; j < n_seg; ++j) {
+        itpp_status stt = itpp_detail_sync_ctl(h);
+        if (stt) return stt;
+        const uint64_t c = h->h_ctl->count[h->h_ctl->cur];
+        snap_n[(size_t)j] = c;
+        if (!snap[(size_t)j].alloc((size_t)c * (kb + 8))) return ITPP_ERR_ALLOC;
+        PKey<W>* sk = snap[(size_t)j].as<PKey<W>>();
+        double* sc = reinterpret_cast<double*>(sk + c);
+        k_adj_snapshot<W><<<grid, 256, 0, st>>>(
+            static_cast<const PKey<W>*>(s.keys[0]), s.coef[0],
+            static_cast<const PKey<W>*>(s.keys[1]), s.coef[1], s.ctl, sk, sc);
+        if (j == 0) k_adj_log<<<1, 32, 0, st>>>(s.ctl, log.as<unsigned long long>(), 0);
+        const int l_end = (j + 1) * K < L ? (j + 1) * K : L;
+        for (int l = j * K; l < l_end; ++l)
+            for (int k = 0; k < G; ++k) {
+                itpp_status e = itpp_detail_launch_gate(h, k);
+                if (e) return e;
+                k_adj_log<<<1, 32, 0, st>>>(s.ctl, log.as<unsigned long long>(),
+                                            (int)((long long)l * G + k + 1));
+            }
+    }
+    itpp_status stt = itpp_detail_sync_ctl(h);
+    if (stt) return stt;
+    std::vector<unsigned long long> cnt_log((size_t)S + 1);
+    if (!chk(cudaMemcpy(cnt_log.data(), log.p, (size_t)(S + 1) * 8, cudaMemcpyDeviceToHost)))
+        return ITPP_ERR_CUDA;
+
+    // ---- value f and the observable table for the seed
+    const size_t tsize = [&] { size_t t = 1; while (t < (size_t)2 * m) t <<= 1; return t; }();
+    DevBuf obs;
+    if (!obs.alloc((size_t)m * W * 16 + (size_t)m * 8 * 4 + tsize * 4 + (size_t)m * 4 + 64))
+        return ITPP_ERR_ALLOC;
+    char* op = obs.as<char>();
+    uint64_t* d_ox = reinterpret_cast<uint64_t*>(op); op += (size_t)m * W * 8;
+    uint64_t* d_oz = reinterpret_cast<uint64_t*>(op); op += (size_t)m * W * 8;
+    double* d_w = reinterpret_cast<double*>(op); op += (size_t)m * 8;
+    double* d_vals = reinterpret_cast<double*>(op); op += (size_t)m * 8;
+    double* d_out = reinterpret_cast<double*>(op); op += (size_t)(m + 1) * 8;
+    double* d_wsum = reinterpret_cast<double*>(op); op += (size_t)m * 8;
+    int* d_tab = reinterpret_cast<int*>(op); op += tsize * 4;
+    int* d_first = reinterpret_cast<int*>(op);
+    if (!chk(cudaMemcpyAsync(d_ox, obs_x, (size_t)m * W * 8, cudaMemcpyHostToDevice, st)) ||
+        !chk(cudaMemcpyAsync(d_oz, obs_z, (size_t)m * W * 8, cudaMemcpyHostToDevice, st)) ||
+        !chk(cudaMemcpyAsync(d_w, seed, (size_t)m * 8, cudaMemcpyHostToDevice, st)))
+        return ITPP_ERR_CUDA;
+    if (!chk(launch_expect(s, d_ox, d_oz, d_w, m, (int)tsize, d_tab, d_first, d_vals, d_out, st)))
+        return ITPP_ERR_CUDA;
+    k_adj_wsum<<<1, 32, 0, st>>>(d_first, d_w, m, d_wsum);
+    double fval = 0;
+    if (!chk(cudaMemcpyAsync(&fval, d_out + m, 8, cudaMemcpyDeviceToHost, st)) ||
+        !chk(cudaStreamSynchronize(st)))
+        return ITPP_ERR_CUDA;
+
+    // ---- arena for the largest segment
+    size_t arena_max = 0, reg_max = 1;
+    for (int j = 0; j < n_seg; ++j) {
+        const long long s0 = (long long)j * K * G;
+        const long long s1 = ((long long)(j + 1) * K < L ? (long long)(j + 1) * K : L) * G;
+        size_t bytes = 0;
+        for (long long q = s0; q <= s1; ++q) {
+            bytes += (size_t)cnt_log[(size_t)q] * (kb + 8);
+            if (q > s0) bytes += (size_t)cnt_log[(size_t)(q - 1)] * 12;
+            reg_max = cnt_log[(size_t)q] > reg_max ? cnt_log[(size_t)q] : reg_max;
+            bytes = (bytes + 255) / 256 * 256 + 3 * 256;
+        }
+        arena_max = bytes > arena_max ? bytes : arena_max;
+    }
+    const int steps_max = K * G;
+    DevBuf arena, mu0, mu1, musave, ctl2, arrs, part, gst, grad;
+    if (!arena.alloc(arena_max) || !mu0.alloc(reg_max * 8) || !mu1.alloc(reg_max * 8) ||
+        !musave.alloc(reg_max * 8) || !ctl2.alloc(sizeof(DevCtl)) ||
+        !arrs.alloc((size_t)(steps_max + 1) * 8 * 3) || !part.alloc((size_t)kRGrid * 8 + 64) ||
+        !gst.alloc((size_t)S * 8) || !grad.alloc((size_t)G * 8))
+        return ITPP_ERR_ALLOC;
+    unsigned long long* a_cnt = arrs.as<unsigned long long>();
+    double* a_rn = reinterpret_cast<double*>(a_cnt + steps_max + 1);
+    unsigned long long* a_id = reinterpret_cast<unsigned long long*>(a_rn + steps_max + 1);
+    double* nu_i = part.as<double>() + kRGrid;
+    DevCtl* c2 = ctl2.as<DevCtl>();
+    if (!chk(cudaMemsetAsync(c2, 0, sizeof(DevCtl), st))) return ITPP_ERR_CUDA;
+    k_adj_gen_copy<<<1, 32, 0, st>>>(c2, s.ctl);
+    double* mu_cur = mu0.as<double>();
+    double* mu_prev = mu1.as<double>();
+
+    for (int j = n_seg - 1; j >= 0; --j) {
+        const long long s0 = (long long)j * K * G;
+        const long long s1 = ((long long)(j + 1) * K < L ? (long long)(j + 1) * K : L) * G;
+        const int R = (int)(s1 - s0);
+        // region layout
+        std::vector<PKey<W>*> rk((size_t)R + 1);
+        std::vector<double*> rc((size_t)R + 1);
+        std::vector<int*> rmap((size_t)R + 1, nullptr);
+        char* ap = arena.as<char>();
+        for (int r = 0; r <= R; ++r) {
+            const size_t c = cnt_log[(size_t)(s0 + r)];
+            rk[(size_t)r] = reinterpret_cast<PKey<W>*>(ap);
+            ap += (c * kb + 255) / 256 * 256;
+            rc[(size_t)r] = reinterpret_cast<double*>(ap);
+            ap += (c * 8 + 255) / 256 * 256;
+            if (r > 0) {
+                const size_t ci = cnt_log[(size_t)(s0 + r - 1)];
+                rmap[(size_t)r] = reinterpret_cast<int*>(ap);
+                ap += (ci * 12 + 255) / 256 * 256;
+            }
+        }
+        // restore the snapshot into region 0 (normalised values, rn = 1)
+        const uint64_t c0 = snap_n[(size_t)j];
+        const PKey<W>* sk = snap[(size_t)j].as<PKey<W>>();
+        const double* sc = reinterpret_cast<const double*>(sk + c0);
+        const unsigned long long c0u = c0;
+        const double one = 1.0;
+        if (!chk(cudaMemcpyAsync(rk[0], sk, c0 * kb, cudaMemcpyDeviceToDevice, st)) ||
+            !chk(cudaMemcpyAsync(rc[0], sc, c0 * 8, cudaMemcpyDeviceToDevice, st)) ||
+            !chk(cudaMemcpyAsync(a_cnt, &c0u, 8, cudaMemcpyHostToDevice, st)) ||
+            !chk(cudaMemcpyAsync(a_rn, &one, 8, cudaMemcpyHostToDevice, st)))
+            return ITPP_ERR_CUDA;
+        // recompute the segment, recording output positions
+        for (int r = 1; r <= R; ++r) {
+            const HostGate& hg = h->gates[(size_t)((s0 + r - 1) % G)];
+            const GateArg<W> g = gate_arg_of<W>(hg);
+            const size_t ci = cnt_log[(size_t)(s0 + r - 1)];
+            const size_t co = cnt_log[(size_t)(s0 + r)];
+            StepMaps maps{rmap[(size_t)r], rmap[(size_t)r] + ci, rmap[(size_t)r] + 2 * ci,
+                          a_id + r};
+            k_adj_prep<<<1, 32, 0, st>>>(c2, a_cnt, a_rn, r, reg_max);
+            k_adj_insert<W><<<grid, 256, 0, st>>>(rk[(size_t)r - 1], rc[(size_t)r - 1], c2,
+                                                  static_cast<Slot<W>*>(s.table), s.table_slots,
+                                                  g, s.probe_limit);
+            k_adj_main<W><<<s.num_sms * 4, 256, 0, st>>>(
+                rk[(size_t)r - 1], rc[(size_t)r - 1], rk[(size_t)r], rc[(size_t)r], c2,
+                static_cast<const Slot<W>*>(s.table), s.table_slots, g, s.delta, co,
+                s.probe_limit, maps);
+            k_adj_post<<<1, 32, 0, st>>>(c2, s.cap_M, a_cnt, a_rn, r);
+        }
+        // seed of this segment's last state
+        const size_t cR = cnt_log[(size_t)s1];
+        if (j == n_seg - 1) {
+            k_adj_seed<W><<<grid, 256, 0, st>>>(rk[(size_t)R], cR, d_ox, d_oz, d_wsum, d_tab,
+                                                (int)tsize, mu_cur);
+        } else {
+            // carry mu across the boundary by key: the next segment's snapshot
+            const uint64_t cn = snap_n[(size_t)j + 1];
+            const PKey<W>* nk = snap[(size_t)j + 1].as<PKey<W>>();
+            k_adj_remap_insert<W><<<grid, 256, 0, st>>>(nk, musave.as<double>(), cn,
+                                                        static_cast<Slot<W>*>(s.table),
+                                                        s.table_slots, c2, s.probe_limit);
+            k_adj_remap_lookup<W><<<grid, 256, 0, st>>>(rk[(size_t)R], cR, cn, mu_cur,
+                                                        static_cast<const Slot<W>*>(s.table),
+                                                        s.table_slots, c2, s.probe_limit);
+            k_adj_bump_gen<<<1, 32, 0, st>>>(c2);
+        }
+        // reverse sweep over the segment
+        for (int r = R; r >= 1; --r) {
+            const HostGate& hg = h->gates[(size_t)((s0 + r - 1) % G)];
+            const size_t ci = cnt_log[(size_t)(s0 + r - 1)];
+            const size_t co = cnt_log[(size_t)(s0 + r)];
+            k_adj_dot<<<kRGrid, kRB, 0, st>>>(rc[(size_t)r], mu_cur, co, a_id + r, a_rn + r,
+                                              part.as<double>());
+            k_adj_dot_final<<<1, kRB, 0, st>>>(part.as<double>(), kRGrid, a_rn + r, nu_i);
+            k_adj_back<W><<<kRGrid, kRB, 0, st>>>(
+                rk[(size_t)r - 1], rc[(size_t)r - 1], ci, a_rn + r - 1, rmap[(size_t)r],
+                rmap[(size_t)r] + ci, rmap[(size_t)r] + 2 * ci, mu_cur, a_id + r, a_rn + r, nu_i,
+                gate_arg_of<W>(hg), hg.sh, hg.chd, mu_prev, part.as<double>());
+            k_adj_gsum<<<1, kRB, 0, st>>>(part.as<double>(), kRGrid, gst.as<double>(),
+                                          s0 + r - 1);
+            double* t = mu_cur; mu_cur = mu_prev; mu_prev = t;
+        }
+        // mu on the snapshot order, for the previous segment
+        if (!chk(cudaMemcpyAsync(musave.p, mu_cur, c0 * 8, cudaMemcpyDeviceToDevice, st)))
+            return ITPP_ERR_CUDA;
+        if (!chk(cudaGetLastError())) return ITPP_ERR_CUDA;
+    }
+    k_adj_params<<<1, 256, 0, st>>>(gst.as<double>(), L, G, h->dtau, grad.as<double>());
+    k_adj_gen_copy<<<1, 32, 0, st>>>(s.ctl, c2);
+    int c2_status = 0;
+    if (!chk(cudaMemcpyAsync(grad_alpha, grad.p, (size_t)G * 8, cudaMemcpyDeviceToHost, st)) ||
+        !chk(cudaMemcpyAsync(&c2_status, &c2->status, sizeof(int), cudaMemcpyDeviceToHost, st)) ||
+        !chk(cudaStreamSynchronize(st)))
+        return ITPP_ERR_CUDA;
+    if (c2_status) return (itpp_status)c2_status;
+    if (value) *value = fval;
+    return ITPP_OK;
+}
+
+}  // namespace
+
+extern "C" itpp_status itpp_adjoint(itpp_handle h, int n_layers, int ckpt_every,
+                                    const uint64_t* obs_x, const uint64_t* obs_z,
+                                    const double* seed, int m, double* grad_alpha,
+                                    double* value) {
+    if (!h || n_layers < 1 || ckpt_every < 1 || !obs_x || !obs_z || !seed || !grad_alpha ||
+        m < 1 || m > 65536)
+        return ITPP_ERR_ARG;
+    if (h->s.cap_policy != 0 || h->gates.empty()) return ITPP_ERR_ARG;
+    if (h->sticky) return h->sticky;
+    itpp_status st = h->s.W == 1
+        ? adjoint_w<1>(h, n_layers, ckpt_every, obs_x, obs_z, seed, m, grad_alpha, value)
+        : adjoint_w<2>(h, n_layers, ckpt_every, obs_x, obs_z, seed, m, grad_alpha, value);
+    if (st == ITPP_ERR_CUDA) h->sticky = st;
+    return st;
+}
+
+extern "C" itpp_status itpp_set_alpha(itpp_handle h, const double* alpha) {
+    if (!h || !alpha) return ITPP_ERR_ARG;
+    for (size_t k = 0; k < h->gates.size(); ++k)
+        if (!std::isfinite(alpha[k])) return ITPP_ERR_ARG;
+    cudaStreamSynchronize(h->stream);
+    for (size_t k = 0; k < h->gates.size(); ++k) {
+        HostGate& g = h->gates[k];
+        const double theta = alpha[k] * h->dtau;
+        g.ch = std::cosh(theta);
+        g.msh = -std::sinh(theta);
+        g.sh = std::sinh(theta);
+        g.chd = std::cosh(theta);
+    }
+    return ITPP_OK;
+}

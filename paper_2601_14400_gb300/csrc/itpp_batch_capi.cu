@@ -1,0 +1,379 @@
+// itpp_batch_capi.cu -- C ABI of the batched propagation (include/itpp.h):
+// many independent ITPP instances advanced in shared launches, one CUDA
+// graph per Trotter layer.
+#include <cmath>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "itpp.h"
+#include "itpp_common.cuh"
+#include "itpp_launch.h"
+
+using namespace itpp;
+
+struct itpp_batch_ctx {
+    BatchState s;
+    std::vector<int> n;        // sites per instance
+    std::vector<int> n_gates;  // gates per layer per instance
+    cudaStream_t stream = nullptr;
+    bool own_stream = false;
+    cudaGraphExec_t layer = nullptr;
+    std::vector<int> h_status;
+    itpp_status sticky = ITPP_OK;
+    void* obs_mem = nullptr;
+    size_t obs_bytes = 0;
+    uint64_t launches = 0;
+    std::vector<unsigned char> h_ctl;   // one DevCtl head, for reads
+};
+
+namespace {
+
+constexpr size_t kHead = offsetof(DevCtl, sel_hist);
+
+uint64_t next_pow2(uint64_t v) {
+    uint64_t s = 1;
+    while (s < v) s <<= 1;
+    return s;
+}
+
+bool bits_ok(int n, int W, const uint64_t* x) {
+    for (int w = 0; w < W; ++w) {
+        const int lo = 64 * w;
+        if (n >= lo + 64) continue;
+        const uint64_t top = (n <= lo) ? ~0ULL : (~0ULL << (n - lo));
+        if (x[w] & top) return false;
+    }
+    return true;
+}
+
+void free_batch(itpp_batch_ctx* h) {
+    BatchState& s = h->s;
+    for (int i = 0; i < 2; ++i) {
+        if (s.keys[i]) cudaFree(s.keys[i]);
+        if (s.coef[i]) cudaFree(s.coef[i]);
+    }
+    if (s.table) cudaFree(s.table);
+    if (s.ctls) cudaFree(s.ctls);
+    if (s.gates) cudaFree(s.gates);
+    if (s.n_gates) cudaFree(s.n_gates);
+    if (s.item_prefix) cudaFree(s.item_prefix);
+    if (h->obs_mem) cudaFree(h->obs_mem);
+    if (h->layer) cudaGraphExecDestroy(h->layer);
+    if (h->own_stream && h->stream) cudaStreamDestroy(h->stream);
+}
+
+// Single-propagation view of instance b (for export, expectation, import).
+DeviceState view(const itpp_batch_ctx* h, int b) {
+    const BatchState& s = h->s;
+    DeviceState d;
+    d.n = h->n[(size_t)b];
+    d.W = s.W;
+    const size_t kb = (size_t)s.buf_cap * 16 * s.W;
+    for (int i = 0; i < 2; ++i) {
+        d.keys[i] = static_cast<char*>(s.keys[i]) + (size_t)b * kb;
+        d.coef[i] = s.coef[i] + (size_t)b * s.buf_cap;
+    }
+    d.table = static_cast<char*>(s.table) + (size_t)b * s.table_slots * (s.W == 1 ? 32 : 64);
+    d.table_slots = s.table_slots;
+    d.ctl = s.ctls + b;
+    d.cap_M = s.cap_M;
+    d.buf_cap = s.buf_cap;
+    d.cap_policy = s.cap_policy;
+    d.delta = s.delta;
+    d.num_sms = s.num_sms;
+    d.load_pct = s.load_pct;
+    d.probe_limit = s.probe_limit;
+    return d;
+}
+
+template <int W>
+void fill_gate(void* dst, const uint64_t* qx, const uint64_t* qz, double alpha, double dtau) {
+    GateArg<W> g;
+    std::memset(&g, 0, sizeof(g));
+    int yy = 0;
+    for (int w = 0; w < W; ++w) {
+        g.qx[w] = qx[w];
+        g.qz[w] = qz[w];
+        uint64_t v = qx[w] & qz[w];
+        while (v) { v &= v - 1; ++yy; }
+    }
+    const double theta = alpha * dtau;
+    g.ch = std::cosh(theta);
+    g.msh = -std::sinh(theta);
+    g.qyy = yy & 3;
+    std::memcpy(dst, &g, sizeof(g));
+}
+
+itpp_status read_head(itpp_batch_ctx* h, int b, DevCtl* out) {
+    if (cudaMemcpyAsync(out, h->s.ctls + b, kHead, cudaMemcpyDeviceToHost, h->stream) !=
+            cudaSuccess ||
+        cudaStreamSynchronize(h->stream) != cudaSuccess) {
+        h->sticky = ITPP_ERR_CUDA;
+        return ITPP_ERR_CUDA;
+    }
+    return ITPP_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+itpp_status itpp_batch_create(int B, const int* n, const int* n_gates, const uint64_t* gate_x,
+                              const uint64_t* gate_z, const double* alpha, double dtau,
+                              const itpp_params* p, void* cuda_stream, itpp_batch_handle* out) {
+    if (!out || !p || !n || !n_gates || B < 1 || B > 65535) return ITPP_ERR_ARG;
+    if (!std::isfinite(dtau) || !(p->delta >= 0.0) || !std::isfinite(p->delta)) return ITPP_ERR_ARG;
+    if (p->cap_M < 1 || p->cap_M > (1ULL << 31)) return ITPP_ERR_ARG;
+    if (p->cap_policy != 0 && p->cap_policy != 1) return ITPP_ERR_ARG;
+    if (p->merge_path != 0) return ITPP_ERR_ARG;
+    int max_n = 0, max_g = 0;
+    long long total_g = 0;
+    for (int b = 0; b < B; ++b) {
+        if (n[b] < 1 || n[b] > 128 || n_gates[b] < 0) return ITPP_ERR_ARG;
+        max_n = n[b] > max_n ? n[b] : max_n;
+        max_g = n_gates[b] > max_g ? n_gates[b] : max_g;
+        total_g += n_gates[b];
+    }
+    if (total_g > 0 && (!gate_x || !gate_z || !alpha)) return ITPP_ERR_ARG;
+    const int W = (max_n + 63) / 64;
+    {
+        long long k = 0;
+        for (int b = 0; b < B; ++b)
+            for (int j = 0; j < n_gates[b]; ++j, ++k) {
+                if (!std::isfinite(alpha[k])) return ITPP_ERR_ARG;
+                if (!bits_ok(n[b], W, gate_x + k * W) || !bits_ok(n[b], W, gate_z + k * W))
+                    return ITPP_ERR_ARG;
+            }
+    }
+    itpp_batch_ctx* h = new (std::nothrow) itpp_batch_ctx;
+    if (!h) return ITPP_ERR_ALLOC;
+    h->n.assign(n, n + B);
+    h->n_gates.assign(n_gates, n_gates + B);
+    h->stream = static_cast<cudaStream_t>(cuda_stream);
+    if (!h->stream) {
+        if (cudaStreamCreateWithFlags(&h->stream, cudaStreamNonBlocking) != cudaSuccess) {
+            delete h;
+            return ITPP_ERR_CUDA;
+        }
+        h->own_stream = true;
+    }
+    BatchState& s = h->s;
+    s.B = B;
+    s.W = W;
+    s.max_gates = max_g;
+    s.cap_M = p->cap_M;
+    s.buf_cap = 2 * p->cap_M;
+    s.cap_policy = p->cap_policy;
+    s.delta = p->delta;
+    s.load_pct = p->table_load_pct ? p->table_load_pct : 50;
+    if (s.load_pct < 10 || s.load_pct > 75) { free_batch(h); delete h; return ITPP_ERR_ARG; }
+    const int load_for_size = s.load_pct < 50 ? s.load_pct : 50;
+    const uint64_t need = (p->cap_M * 100 + load_for_size - 1) / load_for_size;
+    s.table_slots = next_pow2(need < 256 ? 256 : need);
+    int dev = 0, sms = 1;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    s.num_sms = sms;
+
+    const size_t gsz = W == 1 ? sizeof(GateArg<1>) : sizeof(GateArg<2>);
+    std::vector<unsigned char> gates((size_t)B * (max_g > 0 ? max_g : 1) * gsz, 0);
+    {
+        long long k = 0;
+        for (int b = 0; b < B; ++b)
+            for (int j = 0; j < n_gates[b]; ++j, ++k) {
+                void* dst = gates.data() + ((size_t)b * max_g + j) * gsz;
+                if (W == 1) fill_gate<1>(dst, gate_x + k * W, gate_z + k * W, alpha[k], dtau);
+                else fill_gate<2>(dst, gate_x + k * W, gate_z + k * W, alpha[k], dtau);
+            }
+    }
+    const size_t slot = W == 1 ? 32 : 64;
+    bool ok = true;
+    for (int i = 0; i < 2 && ok; ++i) {
+        ok &= cudaMalloc(&s.keys[i], (size_t)B * s.buf_cap * 16 * W) == cudaSuccess;
+        ok &= ok && cudaMalloc(reinterpret_cast<void**>(&s.coef[i]), (size_t)B * s.buf_cap * 8) ==
+                        cudaSuccess;
+    }
+    ok &= ok && cudaMalloc(&s.table, (size_t)B * s.table_slots * slot) == cudaSuccess;
+    ok &= ok && cudaMalloc(reinterpret_cast<void**>(&s.ctls), (size_t)B * sizeof(DevCtl)) == cudaSuccess;
+    ok &= ok && cudaMalloc(&s.gates, gates.size()) == cudaSuccess;
+    ok &= ok && cudaMalloc(reinterpret_cast<void**>(&s.n_gates), (size_t)B * sizeof(int)) == cudaSuccess;
+    ok &= ok && cudaMalloc(reinterpret_cast<void**>(&s.item_prefix),
+                           4 * (size_t)(B + 1) * sizeof(unsigned long long)) == cudaSuccess;
+    if (!ok) {
+        cudaGetLastError();
+        free_batch(h);
+        delete h;
+        return ITPP_ERR_ALLOC;
+    }
+    s.tile_prefix = s.item_prefix + (B + 1);
+    s.cap_prefix = s.tile_prefix + (B + 1);
+    s.ccap_prefix = s.cap_prefix + (B + 1);
+    ok &= cudaMemcpyAsync(s.gates, gates.data(), gates.size(), cudaMemcpyHostToDevice, h->stream) == cudaSuccess;
+    ok &= cudaMemcpyAsync(s.n_gates, n_gates, (size_t)B * sizeof(int), cudaMemcpyHostToDevice, h->stream) == cudaSuccess;
+    ok &= cudaMemsetAsync(s.table, 0, (size_t)B * s.table_slots * slot, h->stream) == cudaSuccess;
+    ok &= cudaMemsetAsync(s.ctls, 0, (size_t)B * sizeof(DevCtl), h->stream) == cudaSuccess;
+    ok &= cudaMemsetAsync(s.item_prefix, 0, 4 * (size_t)(B + 1) * sizeof(unsigned long long), h->stream) == cudaSuccess;
+    for (int b = 0; b < B && ok; ++b) {
+        DeviceState d = view(h, b);
+        ok &= cudaMemcpyAsync(&d.ctl->buf_cap, &s.buf_cap, sizeof(s.buf_cap),
+                              cudaMemcpyHostToDevice, h->stream) == cudaSuccess;
+        ok &= launch_reset_identity(d, h->stream) == cudaSuccess;
+    }
+    ok &= cudaStreamSynchronize(h->stream) == cudaSuccess;
+    if (!ok) {
+        free_batch(h);
+        delete h;
+        return ITPP_ERR_CUDA;
+    }
+    h->h_ctl.resize(sizeof(DevCtl));
+    *out = h;
+    return ITPP_OK;
+}
+
+itpp_status itpp_batch_destroy(itpp_batch_handle h) {
+    if (!h) return ITPP_OK;
+    cudaStreamSynchronize(h->stream);
+    free_batch(h);
+    delete h;
+    return ITPP_OK;
+}
+
+itpp_status itpp_batch_apply_trotter_layer(itpp_batch_handle h, int n_layers) {
+    if (!h || n_layers < 0) return ITPP_ERR_ARG;
+    if (h->sticky) return h->sticky;
+    if (!h->layer && n_layers > 0) {
+        // capture one layer: every gate step, all instances per launch
+        cudaGraph_t g = nullptr;
+        if (cudaStreamBeginCapture(h->stream, cudaStreamCaptureModeThreadLocal) != cudaSuccess)
+            return h->sticky = ITPP_ERR_CUDA;
+        cudaError_t e = cudaSuccess;
+        for (int step = 0; step < h->s.max_gates && e == cudaSuccess; ++step)
+            e = launch_batch_step(h->s, step, h->stream);
+        cudaError_t e2 = cudaStreamEndCapture(h->stream, &g);
+        if (e != cudaSuccess || e2 != cudaSuccess || !g) {
+            if (g) cudaGraphDestroy(g);
+            cudaGetLastError();
+            return h->sticky = ITPP_ERR_CUDA;
+        }
+        e = cudaGraphInstantiate(&h->layer, g, 0);
+        cudaGraphDestroy(g);
+        if (e != cudaSuccess) return h->sticky = ITPP_ERR_CUDA;
+    }
+    for (int l = 0; l < n_layers; ++l) {
+        if (cudaGraphLaunch(h->layer, h->stream) != cudaSuccess) return h->sticky = ITPP_ERR_CUDA;
+        h->launches += (uint64_t)h->s.max_gates * batch_step_launches(h->s);
+    }
+    return ITPP_OK;
+}
+
+itpp_status itpp_batch_get_counts(itpp_batch_handle h, uint64_t* counts, int* statuses) {
+    if (!h || !counts) return ITPP_ERR_ARG;
+    DevCtl* c = reinterpret_cast<DevCtl*>(h->h_ctl.data());
+    itpp_status first = ITPP_OK;
+    for (int b = 0; b < h->s.B; ++b) {
+        itpp_status st = read_head(h, b, c);
+        if (st) return st;
+        counts[b] = c->count[c->cur];
+        if (statuses) statuses[b] = c->status;
+        if (!first && c->status) first = (itpp_status)c->status;
+    }
+    return first;
+}
+
+itpp_status itpp_batch_synchronize(itpp_batch_handle h) {
+    if (!h) return ITPP_ERR_ARG;
+    if (cudaStreamSynchronize(h->stream) != cudaSuccess) return h->sticky = ITPP_ERR_CUDA;
+    std::vector<uint64_t> counts((size_t)h->s.B);
+    return itpp_batch_get_counts(h, counts.data(), nullptr);
+}
+
+itpp_status itpp_batch_get_stats(itpp_batch_handle h, int b, itpp_stats* o) {
+    if (!h || !o || b < 0 || b >= h->s.B) return ITPP_ERR_ARG;
+    DevCtl* c = reinterpret_cast<DevCtl*>(h->h_ctl.data());
+    itpp_status st = read_head(h, b, c);
+    if (st) return st;
+    o->gates_applied = c->stat_gates;
+    o->terms_in = c->stat_in;
+    o->terms_out = c->stat_out;
+    o->peak_terms = c->stat_peak;
+    o->cap_events = c->stat_cap;
+    o->count = c->count[c->cur];
+    o->table_probes = c->stat_probes;
+    o->kernel_launches = h->launches;
+    return (itpp_status)c->status;
+}
+
+itpp_status itpp_batch_get_terms(itpp_batch_handle h, int b, uint64_t* x, uint64_t* z, double* cc,
+                                 uint64_t capacity, uint64_t* count) {
+    if (!h || !count || b < 0 || b >= h->s.B) return ITPP_ERR_ARG;
+    DevCtl* c = reinterpret_cast<DevCtl*>(h->h_ctl.data());
+    itpp_status st = read_head(h, b, c);
+    if (st) return st;
+    if (c->status) return (itpp_status)c->status;
+    const uint64_t n = c->count[c->cur];
+    *count = n;
+    if (capacity < n) return ITPP_ERR_CAPACITY;
+    if (n == 0) return ITPP_OK;
+    if (!x || !z || !cc) return ITPP_ERR_ARG;
+    DeviceState d = view(h, b);
+    const int o = c->cur ^ 1;
+    uint64_t* dx = static_cast<uint64_t*>(d.keys[o]);
+    uint64_t* dz = dx + n * d.W;
+    double* dc = d.coef[o];
+    const size_t kb = (size_t)n * d.W * 8;
+    if (launch_export(d, dx, dz, dc, h->stream) != cudaSuccess ||
+        cudaMemcpyAsync(x, dx, kb, cudaMemcpyDeviceToHost, h->stream) != cudaSuccess ||
+        cudaMemcpyAsync(z, dz, kb, cudaMemcpyDeviceToHost, h->stream) != cudaSuccess ||
+        cudaMemcpyAsync(cc, dc, (size_t)n * 8, cudaMemcpyDeviceToHost, h->stream) != cudaSuccess ||
+        cudaStreamSynchronize(h->stream) != cudaSuccess)
+        return h->sticky = ITPP_ERR_CUDA;
+    return ITPP_OK;
+}
+
+itpp_status itpp_batch_expect(itpp_batch_handle h, int b, const uint64_t* obs_x,
+                              const uint64_t* obs_z, const double* obs_w, int m, double* out) {
+    if (!h || b < 0 || b >= h->s.B || !obs_x || !obs_z || !obs_w || !out || m < 1 || m > 65536)
+        return ITPP_ERR_ARG;
+    if (h->sticky) return h->sticky;
+    const int W = h->s.W;
+    for (int j = 0; j < m; ++j)
+        if (!bits_ok(h->n[(size_t)b], W, obs_x + (size_t)j * W) ||
+            !bits_ok(h->n[(size_t)b], W, obs_z + (size_t)j * W))
+            return ITPP_ERR_ARG;
+    const size_t tsize = next_pow2((uint64_t)2 * m);
+    const size_t need = (size_t)m * W * 16 + (size_t)m * 8 * 2 + (size_t)(m + 1) * 8 + tsize * 4 +
+                        (size_t)m * 4 + 256;
+    if (need > h->obs_bytes) {
+        if (h->obs_mem) cudaFree(h->obs_mem);
+        h->obs_mem = nullptr;
+        h->obs_bytes = 0;
+        if (cudaMalloc(&h->obs_mem, need) != cudaSuccess) return ITPP_ERR_ALLOC;
+        h->obs_bytes = need;
+    }
+    char* p = static_cast<char*>(h->obs_mem);
+    uint64_t* ox = reinterpret_cast<uint64_t*>(p); p += (size_t)m * W * 8;
+    uint64_t* oz = reinterpret_cast<uint64_t*>(p); p += (size_t)m * W * 8;
+    double* ow = reinterpret_cast<double*>(p); p += (size_t)m * 8;
+    double* vals = reinterpret_cast<double*>(p); p += (size_t)m * 8;
+    double* res = reinterpret_cast<double*>(p); p += (size_t)(m + 1) * 8;
+    int* tab = reinterpret_cast<int*>(p); p += tsize * 4;
+    int* first = reinterpret_cast<int*>(p);
+    std::vector<double> buf((size_t)m + 1);
+    DeviceState d = view(h, b);
+    if (cudaMemcpyAsync(ox, obs_x, (size_t)m * W * 8, cudaMemcpyHostToDevice, h->stream) != cudaSuccess ||
+        cudaMemcpyAsync(oz, obs_z, (size_t)m * W * 8, cudaMemcpyHostToDevice, h->stream) != cudaSuccess ||
+        cudaMemcpyAsync(ow, obs_w, (size_t)m * 8, cudaMemcpyHostToDevice, h->stream) != cudaSuccess ||
+        launch_expect(d, ox, oz, ow, m, (int)tsize, tab, first, vals, res, h->stream) != cudaSuccess ||
+        cudaMemcpyAsync(buf.data(), res, ((size_t)m + 1) * 8, cudaMemcpyDeviceToHost, h->stream) != cudaSuccess ||
+        cudaStreamSynchronize(h->stream) != cudaSuccess)
+        return h->sticky = ITPP_ERR_CUDA;
+    DevCtl* c = reinterpret_cast<DevCtl*>(h->h_ctl.data());
+    itpp_status st = read_head(h, b, c);
+    if (st) return st;
+    if (c->status) return (itpp_status)c->status;
+    *out = buf[(size_t)m];
+    return ITPP_OK;
+}
+
+}  // extern "C"

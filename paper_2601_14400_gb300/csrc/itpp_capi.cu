@@ -10,44 +10,10 @@
 
 #include "itpp.h"
 #include "itpp_common.cuh"
+#include "itpp_ctx.h"
 #include "itpp_launch.h"
 
 using namespace itpp;
-
-namespace {
-
-constexpr int kKinds = 4;
-constexpr size_t kCtlHead = offsetof(DevCtl, sel_hist);
-
-struct EventPair {
-    cudaEvent_t a, b;
-};
-
-}  // namespace
-
-struct itpp_ctx {
-    DeviceState s;
-    std::vector<HostGate> gates;
-    double dtau = 0;
-    itpp_params p{};
-    cudaStream_t stream = nullptr;
-    int device = 0;
-    itpp_status sticky = ITPP_OK;
-    DevCtl* h_ctl = nullptr;   // pinned mirror of the control block head
-    // expectation scratch
-    void* obs_mem = nullptr;
-    size_t obs_bytes = 0;
-    // sorted merge scratch
-    void* sort_mem = nullptr;
-    uint64_t sort_bytes = 0;
-    uint64_t launches = 0;   // kernels launched by this handle
-    // profiling
-    bool prof = false;
-    std::vector<EventPair> ev[kKinds];
-    size_t ev_used[kKinds] = {0, 0, 0, 0};
-    double prof_ms[kKinds] = {0, 0, 0, 0};
-    uint64_t prof_n[kKinds] = {0, 0, 0, 0};
-};
 
 namespace {
 
@@ -213,6 +179,9 @@ itpp_status check_obs_args(itpp_ctx* h, const uint64_t* ox, const uint64_t* oz, 
 
 }  // namespace
 
+itpp_status itpp_detail_sync_ctl(itpp_ctx* h) { return sync_ctl(h); }
+itpp_status itpp_detail_launch_gate(itpp_ctx* h, int k) { return launch_one_gate(h, k); }
+
 extern "C" {
 
 const char* itpp_status_string(itpp_status s) {
@@ -354,6 +323,13 @@ itpp_status itpp_apply_trotter_layer(itpp_handle h, int n_layers) {
             if (st) return st;
         }
     return ITPP_OK;
+}
+
+itpp_status itpp_reset(itpp_handle h) {
+    if (!h) return ITPP_ERR_ARG;
+    if (h->sticky == ITPP_ERR_CUDA) return h->sticky;
+    h->sticky = ITPP_OK;
+    return launch_reset_identity(h->s, h->stream) == cudaSuccess ? ITPP_OK : cuda_fail(h);
 }
 
 itpp_status itpp_truncate(itpp_handle h, double delta) {

@@ -60,4 +60,29 @@ cudaError_t launch_truncate(const DeviceState& s, double delta, cudaStream_t st)
 // Reset the control block (state = identity in buffer 0).
 cudaError_t launch_reset_identity(const DeviceState& s, cudaStream_t st);
 
+// Many independent propagations sharing launches (itpp_batch.cu).  Instance
+// b owns the slices [b*buf_cap, (b+1)*buf_cap) of both state buffers,
+// [b*table_slots, ...) of the table and control block ctls[b].
+struct BatchState {
+    int B = 0, W = 1, max_gates = 0;
+    void* keys[2] = {nullptr, nullptr};
+    double* coef[2] = {nullptr, nullptr};
+    void* table = nullptr;
+    DevCtl* ctls = nullptr;
+    void* gates = nullptr;               // GateArg<W>[B * max_gates]
+    int* n_gates = nullptr;              // [B]
+    unsigned long long* item_prefix = nullptr;   // [B + 1] each
+    unsigned long long* tile_prefix = nullptr;
+    unsigned long long* cap_prefix = nullptr;
+    unsigned long long* ccap_prefix = nullptr;
+    uint64_t cap_M = 0, buf_cap = 0, table_slots = 0;
+    int cap_policy = 0;
+    double delta = 0;
+    int num_sms = 1, load_pct = 50, probe_limit = 4096;
+};
+
+// Gate `step` of the layer for every instance that has one.
+cudaError_t launch_batch_step(const BatchState& s, int step, cudaStream_t st);
+int batch_step_launches(const BatchState& s);
+
 }  // namespace itpp

@@ -1,0 +1,92 @@
+"""GPU adjoint (frozen-support gradients) vs the oracle's adjoint.
+
+The oracle's adjoint is pinned on the CPU against central differences of the
+frozen forward, the dense Trotter derivative and the exact thermal
+derivative; here the GPU sweep must match it to 1e-10 of the largest
+gradient component (the reductions run in a different order).
+"""
+import numpy as np
+import pytest
+
+import oracle
+import workloads as wl
+
+pytestmark = pytest.mark.gpu
+
+itpp = pytest.importorskip("paper_2601_14400_gb300")
+torch = pytest.importorskip("torch")
+
+
+def _both(H, dtau, delta, layers, obs, ckpt):
+    g = itpp.Propagator(H.n, H.gate_x, H.gate_z, H.alpha, dtau, delta, 1 << 20)
+    f_g, grad_g = g.adjoint(layers, obs, ckpt_every=ckpt)
+    o = oracle.Oracle(H.n, H.gate_x, H.gate_z, H.alpha, dtau, delta)
+    f_o, grad_o = oracle.FrozenAdjoint(o, layers).grad_alpha(obs, H.n_gates)
+    return g, (f_g, grad_g), (f_o, grad_o)
+
+
+def _close(a, b, tol=1e-10):
+    scale = max(np.max(np.abs(b)), 1e-300)
+    assert np.max(np.abs(a - b)) <= tol * scale, (np.max(np.abs(a - b)), scale)
+
+
+@pytest.mark.parametrize("obs_kind", ["zz", "energy"])
+def test_adjoint_n10_subcase_matches_oracle(obs_kind):
+    H = wl.adjoint_chain(10)
+    O = (wl.zz_observables(10, [(4, 5)])[0] if obs_kind == "zz"
+         else wl.energy_observable(H))
+    g, (f_g, d_g), (f_o, d_o) = _both(H, 0.02, 1e-6, 5, O, ckpt=2)
+    assert abs(f_g - f_o) <= 1e-12 * max(1.0, abs(f_o))
+    _close(d_g, d_o)
+
+
+def test_adjoint_checkpoint_interval_does_not_change_the_gradient():
+    H = wl.tfim_1d(8, 1.0, 0.8, periodic=True)
+    O = wl.zz_observables(8, [(0, 1)])[0]
+    grads = []
+    for ck in (1, 2, 5):
+        g = itpp.Propagator(H.n, H.gate_x, H.gate_z, H.alpha, 0.05, 1e-6, 1 << 18)
+        grads.append(g.adjoint(5, O, ckpt_every=ck)[1])
+    _close(grads[1], grads[0], 1e-13)
+    _close(grads[2], grads[0], 1e-13)
+
+
+def test_adjoint_two_words_matches_oracle():
+    H = wl.random_pauli_hamiltonian(70, 14, 9, max_weight=3)
+    O = wl.Observable(70, H.gate_x[:3].copy(), H.gate_z[:3].copy(), np.array([0.7, -1.1, 0.4]))
+    g, (f_g, d_g), (f_o, d_o) = _both(H, 0.1, 1e-4, 3, O, ckpt=1)
+    _close(d_g, d_o)
+
+
+def test_adjoint_leaves_the_forward_state():
+    H = wl.tfim_1d(6, 1.0, 1.0)
+    O = wl.energy_observable(H)
+    g = itpp.Propagator(H.n, H.gate_x, H.gate_z, H.alpha, 0.05, 1e-8, 1 << 16)
+    f, _ = g.adjoint(4, O, ckpt_every=2)
+    o = oracle.Oracle(H.n, H.gate_x, H.gate_z, H.alpha, 0.05, 1e-8)
+    o.apply_layers(4)
+    from tests._compare import assert_same_state
+    assert_same_state(g.terms(), o.terms(), "after adjoint")
+    assert abs(f - o.expect(O)) <= 1e-12 * abs(o.expect(O))
+
+
+def test_autograd_energy_gradient_wrt_fields_and_couplings():
+    from paper_2601_14400_gb300.autograd import thermal_coefficients
+    n, dtau, layers = 8, 0.05, 6
+    Jv = torch.tensor(np.linspace(0.9, 1.1, n - 1), dtype=torch.float64, requires_grad=True)
+    hv = torch.tensor(np.linspace(0.8, 1.2, n), dtype=torch.float64, requires_grad=True)
+    H = wl.tfim_1d(n, Jv.detach().numpy(), hv.detach().numpy())
+    prop = itpp.Propagator(H.n, H.gate_x, H.gate_z, H.alpha, dtau, 1e-9, 1 << 18)
+    alpha = torch.cat([-Jv, -hv])                      # Trotter order: bonds, then fields
+    c = thermal_coefficients(alpha, prop, layers, H.gate_x, H.gate_z, ckpt_every=3)
+    energy = (alpha * c).sum()                          # <H> = sum_k alpha_k c_{Q_k}
+    energy.backward()
+    # oracle: explicit term + frozen adjoint, chain rule d alpha / d(J, h) = -1
+    o = oracle.Oracle(H.n, H.gate_x, H.gate_z, H.alpha, dtau, 1e-9)
+    f_o, g_o = oracle.FrozenAdjoint(o, layers).grad_alpha(wl.energy_observable(H), H.n_gates)
+    c_o = o.coeffs(H.gate_x, H.gate_z)
+    d_alpha = c_o + g_o
+    want_J, want_h = -d_alpha[:n - 1], -d_alpha[n - 1:]
+    assert abs(float(energy) - f_o) <= 1e-12 * abs(f_o)
+    _close(Jv.grad.numpy(), want_J)
+    _close(hv.grad.numpy(), want_h)
