@@ -236,9 +236,10 @@ itpp_status itpp_set_alpha(itpp_handle h, const double* alpha);
  *   obs_x/z, w   host, m observable strings and weights (w_j = df/dc_{P_j}).
  *   grad_alpha   host, n_gates: df/dalpha_k summed over the layers.
  *   value        host or NULL: f.
- * Requires cap_policy 0 (threshold truncation only).  Device memory: one
- * snapshot per segment plus the states and three int32 maps of every step
- * of the largest segment, allocated for the call.  After the call the handle
+ * The kept support includes the term bound: with cap_policy 1 the frozen
+ * support of a step is its top-M set.  Device memory: one snapshot per
+ * segment plus, for every step of the largest segment, its output before and
+ * after the bound and four int32 maps, allocated for the call.  After the call the handle
  * holds the forward's final state.  Synchronising. */
 itpp_status itpp_adjoint(itpp_handle h, int n_layers, int ckpt_every, const uint64_t* obs_x,
                          const uint64_t* obs_z, const double* w, int m, double* grad_alpha,

@@ -10,6 +10,8 @@
 //               = cosh nu_s[P] + s (-sinh) nu_s[Q P]    ([P,Q] = 0)
 //   df/dtheta_s = sum_{[P,Q]=0} u_{s-1}[P] (sinh nu_s[P] - s cosh nu_s[Q P])
 // where mu_s = df/du_s, nu_s = 0 outside S_s and theta_s = alpha_k dtau.
+// S_s is the kept set of step s: after the threshold and, with the top-M
+// bound, after the select.
 //
 // Memory: the forward saves a snapshot every ckpt_every layers; each segment
 // is recomputed from its snapshot into an arena that keeps every step's state
@@ -128,12 +130,65 @@ k_adj_main(const PKey<W>* kin, const double* cin, PKey<W>* kout, double* cout, D
                                    dbits, cap_out, probe_limit, s_scan, &s_base, &probes, maps);
 }
 
-__global__ void k_adj_post(DevCtl* ctl, uint64_t cap_M, unsigned long long* cnt, double* rn,
-                           int r) {
+__global__ void k_adj_post(DevCtl* ctl, uint64_t cap_M, int cap_policy) {
     if (threadIdx.x != 0 || ctl->status) return;
-    post_one(ctl, cap_M, 0);
-    cnt[r] = ctl->count[1];
+    post_one(ctl, cap_M, cap_policy);   // output (buffer 1) above the bound -> select
+    ctl->count[0] = 0;                  // the compacted copy is counted here
+    ctl->norm[0] = ctl->norm[1];
+    ctl->rnorm[0] = ctl->rnorm[1];
+}
+
+// Kept terms of step r (all of them, or the top-M select's when it fired)
+// copied from the step's output into its compact region, recording the
+// compaction map and the identity's position.
+template <int W, int BLOCK>
+__global__ void __launch_bounds__(BLOCK)
+k_adj_compact(const PKey<W>* kpre, const double* cpre, PKey<W>* kout, double* cout,
+              DevCtl* ctl, int* cmap, unsigned long long* id_pos) {
+    __shared__ uint32_t s_scan[BLOCK / 32];
+    __shared__ unsigned long long s_base;
+    if (ctl->status) return;
+    const uint64_t n = live_count(ctl, 1);
+    const bool active = ctl->sel_active;
+    const unsigned long long T = ctl->sel_prefix;
+    const bool all_ties = ctl->sel_k == ctl->sel_ties;
+    PKey<W> tk;
+#pragma unroll
+    for (int w = 0; w < W; ++w) { tk.x[w] = ctl->sel_tie_key[w]; tk.z[w] = ctl->sel_tie_key[W + w]; }
+    const uint64_t tiles = (n + BLOCK - 1) / BLOCK;
+    for (uint64_t t = blockIdx.x; t < tiles; t += gridDim.x) {
+        const uint64_t i = t * BLOCK + threadIdx.x;
+        PKey<W> K;
+        double c = 0;
+        bool keep = false;
+        if (i < n) {
+            K = kpre[i];
+            c = cpre[i];
+            keep = !active || cap_keep(K, c, T, all_ties, tk);
+            if (key_is_zero(K) && !keep) set_status(ctl, ST_TRACE_ZERO, 32);
+        }
+        uint32_t tot;
+        const uint32_t off = block_exclusive_scan<BLOCK>(keep ? 1u : 0u, &tot, s_scan);
+        if (threadIdx.x == 0)
+            s_base = tot ? atomicAdd(&ctl->count[0], (unsigned long long)tot) : 0ULL;
+        __syncthreads();
+        if (i < n) {
+            const uint64_t pos = s_base + off;
+            cmap[i] = keep ? (int)pos : -1;
+            if (keep) {
+                kout[pos] = K;
+                cout[pos] = c;
+                if (key_is_zero(K)) *id_pos = pos;
+            }
+        }
+    }
+}
+
+__global__ void k_adj_after(DevCtl* ctl, unsigned long long* cnt, double* rn, int r) {
+    if (threadIdx.x != 0) return;
+    cnt[r] = ctl->count[0];
     rn[r] = ctl->rnorm[1];
+    ctl->sel_active = 0;
 }
 
 // Seed: mu[i] = sum of the weights of the observable strings equal to key i.
@@ -196,25 +251,31 @@ k_adj_dot_final(const double* partials, int np, const double* rn, double* nu_i) 
 template <int W>
 __global__ void __launch_bounds__(kRB)
 k_adj_back(const PKey<W>* kin, const double* cin, uint64_t n_in, const double* rn_in,
-           const int* self_out, const int* emit_out, const int* part_src, const double* mu_out,
-           const unsigned long long* idpos_out, const double* rn_out, const double* nu_i,
-           GateArg<W> g, double sh, double chd, double* mu_in, double* partials) {
+           const int* self_out, const int* emit_out, const int* part_src, const int* cmap,
+           const double* mu_out, const unsigned long long* idpos_out, const double* rn_out,
+           const double* nu_i, GateArg<W> g, double sh, double chd, double* mu_in,
+           double* partials) {
     __shared__ double s[kRB];
     const double ri = *rn_in, ro = *rn_out, nI = *nu_i;
     const long long id = (long long)*idpos_out;
+    // nu at an output position of the step (before the term bound)
+    auto nu = [&](int pre) -> double {
+        if (pre < 0) return 0.0;
+        const int c = cmap[pre];
+        return c < 0 ? 0.0 : (c == id ? nI : __dmul_rn(mu_out[c], ro));
+    };
     double acc = 0.0;
     for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n_in;
          i += (uint64_t)gridDim.x * blockDim.x) {
         const PKey<W> K = kin[i];
-        const int so = self_out[i];
-        const double vs = so < 0 ? 0.0 : (so == id ? nI : __dmul_rn(mu_out[so], ro));
+        const double vs = nu(self_out[i]);
         if (!commutes(K, g)) {
             mu_in[i] = vs;
         } else {
             const double sg = product_negative(K, g) ? -1.0 : 1.0;
             int po = emit_out[i];
             if (po < 0 && part_src[i] >= 0) po = self_out[part_src[i]];
-            const double vp = po < 0 ? 0.0 : (po == id ? nI : __dmul_rn(mu_out[po], ro));
+            const double vp = nu(po);
             mu_in[i] = __dadd_rn(__dmul_rn(g.ch, vs), __dmul_rn(sg * g.msh, vp));
             const double u = normalised(cin[i], ri, key_is_zero(K));
             acc = __dadd_rn(acc, __dmul_rn(u, __dsub_rn(__dmul_rn(sh, vs),
@@ -363,17 +424,27 @@ itpp_status adjoint_w(itpp_ctx* h, int L, int K, const uint64_t* obs_x, const ui
         !chk(cudaStreamSynchronize(st)))
         return ITPP_ERR_CUDA;
 
-    // ---- arena for the largest segment
+    // ---- arena for the largest segment.  Per step r >= 1: the step's output
+    // before the term bound ("pre", at most 2 * inputs), its kept terms
+    // ("comp", the next step's input), the three output-position maps of the
+    // inputs and the compaction map of the pre terms; region 0 holds the
+    // snapshot.
+    auto round256 = [](size_t b) { return (b + 255) / 256 * 256; };
     size_t arena_max = 0, reg_max = 1;
     for (int j = 0; j < n_seg; ++j) {
         const long long s0 = (long long)j * K * G;
         const long long s1 = ((long long)(j + 1) * K < L ? (long long)(j + 1) * K : L) * G;
         size_t bytes = 0;
         for (long long q = s0; q <= s1; ++q) {
-            bytes += (size_t)cnt_log[(size_t)q] * (kb + 8);
-            if (q > s0) bytes += (size_t)cnt_log[(size_t)(q - 1)] * 12;
-            reg_max = cnt_log[(size_t)q] > reg_max ? cnt_log[(size_t)q] : reg_max;
-            bytes = (bytes + 255) / 256 * 256 + 3 * 256;
+            const size_t c = cnt_log[(size_t)q];
+            bytes += round256(c * kb) + round256(c * 8);
+            if (q > s0) {
+                const size_t ci = cnt_log[(size_t)(q - 1)];
+                bytes += round256(2 * ci * kb) + round256(2 * ci * 8) + round256(ci * 12) +
+                         round256(2 * ci * 4);
+                reg_max = 2 * ci > reg_max ? 2 * ci : reg_max;
+            }
+            reg_max = c > reg_max ? c : reg_max;
         }
         arena_max = bytes > arena_max ? bytes : arena_max;
     }
@@ -381,12 +452,13 @@ itpp_status adjoint_w(itpp_ctx* h, int L, int K, const uint64_t* obs_x, const ui
     DevBuf arena, mu0, mu1, musave, ctl2, arrs, part, gst, grad;
     if (!arena.alloc(arena_max) || !mu0.alloc(reg_max * 8) || !mu1.alloc(reg_max * 8) ||
         !musave.alloc(reg_max * 8) || !ctl2.alloc(sizeof(DevCtl)) ||
-        !arrs.alloc((size_t)(steps_max + 1) * 8 * 3) || !part.alloc((size_t)kRGrid * 8 + 64) ||
+        !arrs.alloc((size_t)(steps_max + 1) * 8 * 4) || !part.alloc((size_t)kRGrid * 8 + 64) ||
         !gst.alloc((size_t)S * 8) || !grad.alloc((size_t)G * 8))
         return ITPP_ERR_ALLOC;
     unsigned long long* a_cnt = arrs.as<unsigned long long>();
     double* a_rn = reinterpret_cast<double*>(a_cnt + steps_max + 1);
     unsigned long long* a_id = reinterpret_cast<unsigned long long*>(a_rn + steps_max + 1);
+    unsigned long long* a_idpre = a_id + steps_max + 1;   // identity position before the bound
     double* nu_i = part.as<double>() + kRGrid;
     DevCtl* c2 = ctl2.as<DevCtl>();
     if (!chk(cudaMemsetAsync(c2, 0, sizeof(DevCtl), st))) return ITPP_ERR_CUDA;
@@ -399,20 +471,26 @@ itpp_status adjoint_w(itpp_ctx* h, int L, int K, const uint64_t* obs_x, const ui
         const long long s1 = ((long long)(j + 1) * K < L ? (long long)(j + 1) * K : L) * G;
         const int R = (int)(s1 - s0);
         // region layout
-        std::vector<PKey<W>*> rk((size_t)R + 1);
-        std::vector<double*> rc((size_t)R + 1);
-        std::vector<int*> rmap((size_t)R + 1, nullptr);
+        std::vector<PKey<W>*> rk((size_t)R + 1), pk((size_t)R + 1, nullptr);
+        std::vector<double*> rc((size_t)R + 1), pc((size_t)R + 1, nullptr);
+        std::vector<int*> rmap((size_t)R + 1, nullptr), cmap((size_t)R + 1, nullptr);
         char* ap = arena.as<char>();
         for (int r = 0; r <= R; ++r) {
             const size_t c = cnt_log[(size_t)(s0 + r)];
             rk[(size_t)r] = reinterpret_cast<PKey<W>*>(ap);
-            ap += (c * kb + 255) / 256 * 256;
+            ap += round256(c * kb);
             rc[(size_t)r] = reinterpret_cast<double*>(ap);
-            ap += (c * 8 + 255) / 256 * 256;
+            ap += round256(c * 8);
             if (r > 0) {
                 const size_t ci = cnt_log[(size_t)(s0 + r - 1)];
+                pk[(size_t)r] = reinterpret_cast<PKey<W>*>(ap);
+                ap += round256(2 * ci * kb);
+                pc[(size_t)r] = reinterpret_cast<double*>(ap);
+                ap += round256(2 * ci * 8);
                 rmap[(size_t)r] = reinterpret_cast<int*>(ap);
-                ap += (ci * 12 + 255) / 256 * 256;
+                ap += round256(ci * 12);
+                cmap[(size_t)r] = reinterpret_cast<int*>(ap);
+                ap += round256(2 * ci * 4);
             }
         }
         // restore the snapshot into region 0 (normalised values, rn = 1)
@@ -431,18 +509,31 @@ itpp_status adjoint_w(itpp_ctx* h, int L, int K, const uint64_t* obs_x, const ui
             const HostGate& hg = h->gates[(size_t)((s0 + r - 1) % G)];
             const GateArg<W> g = gate_arg_of<W>(hg);
             const size_t ci = cnt_log[(size_t)(s0 + r - 1)];
-            const size_t co = cnt_log[(size_t)(s0 + r)];
             StepMaps maps{rmap[(size_t)r], rmap[(size_t)r] + ci, rmap[(size_t)r] + 2 * ci,
-                          a_id + r};
+                          a_idpre + r};
             k_adj_prep<<<1, 32, 0, st>>>(c2, a_cnt, a_rn, r, reg_max);
             k_adj_insert<W><<<grid, 256, 0, st>>>(rk[(size_t)r - 1], rc[(size_t)r - 1], c2,
                                                   static_cast<Slot<W>*>(s.table), s.table_slots,
                                                   g, s.probe_limit);
             k_adj_main<W><<<s.num_sms * 4, 256, 0, st>>>(
-                rk[(size_t)r - 1], rc[(size_t)r - 1], rk[(size_t)r], rc[(size_t)r], c2,
-                static_cast<const Slot<W>*>(s.table), s.table_slots, g, s.delta, co,
+                rk[(size_t)r - 1], rc[(size_t)r - 1], pk[(size_t)r], pc[(size_t)r], c2,
+                static_cast<const Slot<W>*>(s.table), s.table_slots, g, s.delta, 2 * ci,
                 s.probe_limit, maps);
-            k_adj_post<<<1, 32, 0, st>>>(c2, s.cap_M, a_cnt, a_rn, r);
+            k_adj_post<<<1, 32, 0, st>>>(c2, s.cap_M, s.cap_policy);
+            if (s.cap_policy == 1) {
+                DeviceState v = s;
+                v.keys[0] = rk[(size_t)r];
+                v.coef[0] = rc[(size_t)r];
+                v.keys[1] = pk[(size_t)r];
+                v.coef[1] = pc[(size_t)r];
+                v.ctl = c2;
+                v.buf_cap = reg_max;
+                if (!chk(launch_cap_select(v, st))) return ITPP_ERR_CUDA;
+            }
+            k_adj_compact<W, 256><<<grid, 256, 0, st>>>(pk[(size_t)r], pc[(size_t)r],
+                                                        rk[(size_t)r], rc[(size_t)r], c2,
+                                                        cmap[(size_t)r], a_id + r);
+            k_adj_after<<<1, 32, 0, st>>>(c2, a_cnt, a_rn, r);
         }
         // seed of this segment's last state
         const size_t cR = cnt_log[(size_t)s1];
@@ -471,8 +562,9 @@ itpp_status adjoint_w(itpp_ctx* h, int L, int K, const uint64_t* obs_x, const ui
             k_adj_dot_final<<<1, kRB, 0, st>>>(part.as<double>(), kRGrid, a_rn + r, nu_i);
             k_adj_back<W><<<kRGrid, kRB, 0, st>>>(
                 rk[(size_t)r - 1], rc[(size_t)r - 1], ci, a_rn + r - 1, rmap[(size_t)r],
-                rmap[(size_t)r] + ci, rmap[(size_t)r] + 2 * ci, mu_cur, a_id + r, a_rn + r, nu_i,
-                gate_arg_of<W>(hg), hg.sh, hg.chd, mu_prev, part.as<double>());
+                rmap[(size_t)r] + ci, rmap[(size_t)r] + 2 * ci, cmap[(size_t)r], mu_cur,
+                a_id + r, a_rn + r, nu_i, gate_arg_of<W>(hg), hg.sh, hg.chd, mu_prev,
+                part.as<double>());
             k_adj_gsum<<<1, kRB, 0, st>>>(part.as<double>(), kRGrid, gst.as<double>(),
                                           s0 + r - 1);
             double* t = mu_cur; mu_cur = mu_prev; mu_prev = t;
@@ -503,7 +595,7 @@ extern "C" itpp_status itpp_adjoint(itpp_handle h, int n_layers, int ckpt_every,
     if (!h || n_layers < 1 || ckpt_every < 1 || !obs_x || !obs_z || !seed || !grad_alpha ||
         m < 1 || m > 65536)
         return ITPP_ERR_ARG;
-    if (h->s.cap_policy != 0 || h->gates.empty()) return ITPP_ERR_ARG;
+    if (h->gates.empty()) return ITPP_ERR_ARG;
     if (h->sticky) return h->sticky;
     itpp_status st = h->s.W == 1
         ? adjoint_w<1>(h, n_layers, ckpt_every, obs_x, obs_z, seed, m, grad_alpha, value)

@@ -284,7 +284,7 @@ cudaError_t launch_gate_post(const DeviceState& s, cudaStream_t st) {
 }
 
 template <int W>
-static cudaError_t cap_w(const DeviceState& s, cudaStream_t st) {
+static cudaError_t cap_select_w(const DeviceState& s, cudaStream_t st) {
     const int g = stream_grid(s, 256, 8);
     const int shifts[5] = {50, 37, 24, 11, 0};
     for (int p = 0; p < 5; ++p) {
@@ -298,9 +298,21 @@ static cudaError_t cap_w(const DeviceState& s, cudaStream_t st) {
         k_tie_pick<W><<<1, 1024, 0, st>>>(s.ctl, p);
     }
     k_tie_find<W><<<g, 256, 0, st>>>(s.ctl, ties);
+    return cudaGetLastError();
+}
+
+template <int W>
+static cudaError_t cap_w(const DeviceState& s, cudaStream_t st) {
+    cudaError_t e = cap_select_w<W>(s, st);
+    if (e != cudaSuccess) return e;
+    const int g = stream_grid(s, 256, 8);
     k_cap_compact<W, 256><<<g, 256, 0, st>>>(bufs_of<W>(s), s.ctl);
     k_cap_end<<<1, 32, 0, st>>>(s.ctl);
     return cudaGetLastError();
+}
+
+cudaError_t launch_cap_select(const DeviceState& s, cudaStream_t st) {
+    return s.W == 1 ? cap_select_w<1>(s, st) : cap_select_w<2>(s, st);
 }
 
 int cap_launches(const DeviceState& s) { return 5 * 2 + 1 + 8 * s.W * 2 + 3; }

@@ -39,6 +39,9 @@ cudaError_t launch_gate_post(const DeviceState& s, cudaStream_t st);
 // Top-M select and compaction (no-ops on the device when the bound holds).
 cudaError_t launch_cap(const DeviceState& s, cudaStream_t st);
 int cap_launches(const DeviceState& s);
+// The select part only (threshold and tie key in the control block, no
+// compaction): used where the kept set is compacted elsewhere.
+cudaError_t launch_cap_select(const DeviceState& s, cudaStream_t st);
 // Sort-based merge path (children buffer, radix sort, segmented reduce).
 cudaError_t launch_gate_sorted(const DeviceState& s, const HostGate& g, void* scratch,
                                uint64_t scratch_bytes, cudaStream_t st);

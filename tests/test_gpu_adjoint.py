@@ -40,6 +40,20 @@ def test_adjoint_n10_subcase_matches_oracle(obs_kind):
     _close(d_g, d_o)
 
 
+@pytest.mark.parametrize("M", [500, 3000])
+def test_adjoint_with_top_m_bound_matches_oracle(M):
+    # frozen support = the kept top-M set of every step
+    H = wl.adjoint_chain(10)
+    O = wl.energy_observable(H)
+    g = itpp.Propagator(H.n, H.gate_x, H.gate_z, H.alpha, 0.05, 1e-9, M, 1)
+    f_g, d_g = g.adjoint(4, O, ckpt_every=2)
+    assert g.stats()["cap_events"] > 0
+    o = oracle.Oracle(H.n, H.gate_x, H.gate_z, H.alpha, 0.05, 1e-9, M, 1)
+    f_o, d_o = oracle.FrozenAdjoint(o, 4).grad_alpha(O, H.n_gates)
+    assert abs(f_g - f_o) <= 1e-12 * max(1.0, abs(f_o))
+    _close(d_g, d_o)
+
+
 def test_adjoint_checkpoint_interval_does_not_change_the_gradient():
     H = wl.tfim_1d(8, 1.0, 0.8, periodic=True)
     O = wl.zz_observables(8, [(0, 1)])[0]
