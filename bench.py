@@ -54,6 +54,9 @@ def parse():
                     help="override the term bound (2^k); 0 keeps the workload's")
     ap.add_argument("--setup-layers", type=int, default=-1,
                     help="untimed layers before warm-up (-1: until the bound is reached)")
+    ap.add_argument("--block", type=int, default=0, help="threads per CTA of the gate kernels")
+    ap.add_argument("--ipt", type=int, default=0, help="terms per thread per tile")
+    ap.add_argument("--merge-path", type=int, default=0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--mode", default="headline", choices=["headline", "batch", "adjoint"],
@@ -372,7 +375,8 @@ def main():
         itpp.build()
 
     stream = torch.cuda.Stream()
-    g = itpp.Propagator.from_workload(w, stream=stream)
+    g = itpp.Propagator.from_workload(w, stream=stream, block_threads=args.block,
+                                      items_per_thread=args.ipt, merge_path=args.merge_path)
     W = w.H.W
     term_bytes = 16 * W + 8
 

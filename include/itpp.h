@@ -73,9 +73,12 @@ typedef struct {
      *    then z[0..W-1] compared as unsigned), the K-truncation of Sec. II.C
      *    applied only when the bound is exceeded ("adapting"). */
     int cap_policy;
-    /* 0: open-addressing hash merge of the two children of each key (main);
-     * 1: sort-based merge -- all children are sorted by key and equal keys
-     *    reduced.  Both give bit-identical states. */
+    /* How the children of equal strings are found and summed; every path
+     * gives bit-identical states.
+     * 0: partitioned merge (default): the state is scattered into hash
+     *    partitions of the pair key {K, Q.K}, and each partition is merged
+     *    through an open-addressing table in shared memory.
+     * 2: one open-addressing table in global memory for the whole state. */
     int merge_path;
     /* Tuning (0 = library default or the autotuned value):
      * table_load_pct: highest load of the merge table, in percent (10..75).

@@ -125,9 +125,10 @@ k_adj_main(const PKey<W>* kin, const double* cin, PKey<W>* kout, double* cout, D
     const uint64_t mask = table_mask(n, alloc_slots, 50);
     const uint64_t tiles = (n + 511) / 512;
     int probes = 0;
+    const GlobalLookup<W> lk{table, mask, gen, probe_limit, ctl, &probes};
     for (uint64_t t = blockIdx.x; t < tiles; t += gridDim.x)
-        gate_tile<W, 256, 2, true>(t, n, kin, cin, kout, cout, ctl, 0, table, mask, gen, g, rnorm,
-                                   dbits, cap_out, probe_limit, s_scan, &s_base, &probes, maps);
+        gate_tile<W, 256, 2, true>(t, n, kin, cin, kout, cout, ctl, 0, lk, g, rnorm, dbits,
+                                   cap_out, s_scan, &s_base, maps);
 }
 
 __global__ void k_adj_post(DevCtl* ctl, uint64_t cap_M, int cap_policy) {
@@ -379,6 +380,7 @@ itpp_status adjoint_w(itpp_ctx* h, int L, int K, const uint64_t* obs_x, const ui
         if (!snap[(size_t)j].alloc((size_t)c * (kb + 8))) return ITPP_ERR_ALLOC;
         PKey<W>* sk = snap[(size_t)j].as<PKey<W>>();
         double* sc = reinterpret_cast<double*>(sk + c);
+        if (!chk(launch_materialize(s, st))) return ITPP_ERR_CUDA;
         k_adj_snapshot<W><<<grid, 256, 0, st>>>(
             static_cast<const PKey<W>*>(s.keys[0]), s.coef[0],
             static_cast<const PKey<W>*>(s.keys[1]), s.coef[1], s.ctl, sk, sc);
@@ -416,7 +418,8 @@ itpp_status adjoint_w(itpp_ctx* h, int L, int K, const uint64_t* obs_x, const ui
         !chk(cudaMemcpyAsync(d_oz, obs_z, (size_t)m * W * 8, cudaMemcpyHostToDevice, st)) ||
         !chk(cudaMemcpyAsync(d_w, seed, (size_t)m * 8, cudaMemcpyHostToDevice, st)))
         return ITPP_ERR_CUDA;
-    if (!chk(launch_expect(s, d_ox, d_oz, d_w, m, (int)tsize, d_tab, d_first, d_vals, d_out, st)))
+    if (!chk(launch_materialize(s, st)) ||
+        !chk(launch_expect(s, d_ox, d_oz, d_w, m, (int)tsize, d_tab, d_first, d_vals, d_out, st)))
         return ITPP_ERR_CUDA;
     k_adj_wsum<<<1, 32, 0, st>>>(d_first, d_w, m, d_wsum);
     double fval = 0;

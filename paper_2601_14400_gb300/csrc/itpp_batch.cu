@@ -146,11 +146,11 @@ k_b_main(BatchBufs<W> S, int step, double delta, int load_pct, int probe_limit) 
         const uint64_t mask = table_mask(n, S.table_slots, load_pct);
         const uint64_t off = (uint64_t)b * S.buf_cap;
         const GateArg<W> g = S.gates[(size_t)b * S.max_gates + step];
+        const GlobalLookup<W> lk{S.table + (uint64_t)b * S.table_slots, mask, ctl->gen,
+                                 probe_limit, ctl, &probes};
         gate_tile<W, kBlock, kIpt>(t - S.tile_prefix[b], n, S.k[cur] + off, S.c[cur] + off,
-                                   S.k[cur ^ 1] + off, S.c[cur ^ 1] + off, ctl, cur,
-                                   S.table + (uint64_t)b * S.table_slots, mask, ctl->gen, g,
-                                   ctl->rnorm[cur], dbits, S.buf_cap, probe_limit, s_scan,
-                                   &s_base, &probes);
+                                   S.k[cur ^ 1] + off, S.c[cur ^ 1] + off, ctl, cur, lk, g,
+                                   ctl->rnorm[cur], dbits, S.buf_cap, s_scan, &s_base);
         __syncthreads();
     }
 }

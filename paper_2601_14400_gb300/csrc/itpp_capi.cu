@@ -52,6 +52,9 @@ void free_all(itpp_ctx* h) {
         if (h->s.coef[i]) cudaFree(h->s.coef[i]);
     }
     if (h->s.table) cudaFree(h->s.table);
+    if (h->s.part_keys) cudaFree(h->s.part_keys);
+    if (h->s.part_coef) cudaFree(h->s.part_coef);
+    if (h->s.part_cursor) cudaFree(h->s.part_cursor);
     if (h->s.ctl) cudaFree(h->s.ctl);
     if (h->obs_mem) cudaFree(h->obs_mem);
     if (h->sort_mem) cudaFree(h->sort_mem);
@@ -107,7 +110,16 @@ itpp_status sync_ctl(itpp_ctx* h) {
 itpp_status launch_one_gate(itpp_ctx* h, int k) {
     const HostGate& g = h->gates[(size_t)k];
     cudaError_t e = cudaSuccess;
-    {
+    if (h->p.merge_path == 0) {
+        EventPair* ev0 = prof_begin(h, 0);
+        e = launch_part_scatter(h->s, g, h->stream);
+        prof_end(h, ev0);
+        if (e == cudaSuccess) {
+            EventPair* ev1 = prof_begin(h, 1);
+            e = launch_part_merge(h->s, g, h->stream);
+            prof_end(h, ev1);
+        }
+    } else {
         EventPair* ev0 = prof_begin(h, 0);
         e = launch_gate_insert(h->s, g, h->stream);
         prof_end(h, ev0);
@@ -209,7 +221,7 @@ itpp_status itpp_create(int n, const uint64_t* gate_x, const uint64_t* gate_z,
     if (!std::isfinite(dtau) || !(p->delta >= 0.0) || !std::isfinite(p->delta)) return ITPP_ERR_ARG;
     if (p->cap_M < 1 || p->cap_M > (1ULL << 31)) return ITPP_ERR_ARG;
     if (p->cap_policy != 0 && p->cap_policy != 1) return ITPP_ERR_ARG;
-    if (p->merge_path != 0) return ITPP_ERR_ARG;
+    if (p->merge_path != 0 && p->merge_path != 2) return ITPP_ERR_ARG;
     if (p->table_load_pct != 0 && (p->table_load_pct < 10 || p->table_load_pct > 75))
         return ITPP_ERR_ARG;
     if (p->block_threads != 0 && p->block_threads != 128 && p->block_threads != 256 &&
@@ -245,8 +257,11 @@ itpp_status itpp_create(int n, const uint64_t* gate_x, const uint64_t* gate_z,
     s.cap_policy = p->cap_policy;
     s.delta = p->delta;
     s.load_pct = p->table_load_pct ? p->table_load_pct : 50;
-    s.block = p->block_threads ? p->block_threads : 256;
-    s.ipt = p->items_per_thread ? p->items_per_thread : 2;
+    // defaults from the block-shape sweep: 512 x 1 for the partitioned merge,
+    // 256 x 2 for the global-table merge
+    s.block = p->block_threads ? p->block_threads : (p->merge_path == 0 ? 512 : 256);
+    s.ipt = p->items_per_thread ? p->items_per_thread : (p->merge_path == 0 ? 1 : 2);
+    s.merge_deferred = p->merge_path == 0;
     s.probe_limit = 4096;
     const int load_for_size = s.load_pct < 50 ? s.load_pct : 50;
     uint64_t need = (p->cap_M * 100 + load_for_size - 1) / load_for_size;
@@ -278,6 +293,14 @@ itpp_status itpp_create(int n, const uint64_t* gate_x, const uint64_t* gate_z,
     ok &= ok && cudaMalloc(&s.table, s.table_slots * slot_bytes(W)) == cudaSuccess;
     ok &= ok && cudaMalloc(reinterpret_cast<void**>(&s.ctl), sizeof(DevCtl)) == cudaSuccess;
     ok &= ok && cudaMallocHost(reinterpret_cast<void**>(&h->h_ctl), sizeof(DevCtl)) == cudaSuccess;
+    if (ok && p->merge_path == 0) {
+        s.part_cap = p->cap_M + p->cap_M / 2 + 65536;
+        s.part_max = partition_max(W, p->cap_M);
+        ok &= cudaMalloc(&s.part_keys, s.part_cap * 16 * W) == cudaSuccess;
+        ok &= ok && cudaMalloc(reinterpret_cast<void**>(&s.part_coef), s.part_cap * 8) == cudaSuccess;
+        ok &= ok && cudaMalloc(reinterpret_cast<void**>(&s.part_cursor),
+                               (size_t)s.part_max * sizeof(unsigned int)) == cudaSuccess;
+    }
     if (!ok) {
         cudaGetLastError();
         free_all(h);
@@ -335,6 +358,7 @@ itpp_status itpp_reset(itpp_handle h) {
 itpp_status itpp_truncate(itpp_handle h, double delta) {
     if (!h || !(delta >= 0.0) || !std::isfinite(delta)) return ITPP_ERR_ARG;
     if (h->sticky) return h->sticky;
+    if (launch_materialize(h->s, h->stream) != cudaSuccess) return cuda_fail(h);
     return launch_truncate(h->s, delta, h->stream) == cudaSuccess ? ITPP_OK : cuda_fail(h);
 }
 
@@ -368,6 +392,7 @@ itpp_status itpp_get_stats(itpp_handle h, itpp_stats* o) {
 itpp_status itpp_get_terms(itpp_handle h, uint64_t* x, uint64_t* z, double* c,
                            uint64_t capacity, uint64_t* count) {
     if (!h || !count) return ITPP_ERR_ARG;
+    if (!h->sticky && launch_materialize(h->s, h->stream) != cudaSuccess) return cuda_fail(h);
     itpp_status st = sync_ctl(h);
     if (st) return st;
     const uint64_t n = h->h_ctl->count[h->h_ctl->cur];
@@ -422,6 +447,7 @@ itpp_status itpp_expect_device(itpp_handle h, const uint64_t* d_ox, const uint64
     itpp_status st = ensure_obs(h, m, h->s.W);
     if (st) return st;
     ObsPtrs o = obs_layout(h, m, h->s.W);
+    if (launch_materialize(h->s, h->stream) != cudaSuccess) return cuda_fail(h);
     EventPair* ev = prof_begin(h, 3);
     cudaError_t e = launch_expect(h->s, d_ox, d_oz, d_ow, m, o.tsize, o.tab, o.first, o.vals,
                                   d_out, h->stream);
@@ -444,6 +470,7 @@ static itpp_status expect_host(itpp_handle h, const uint64_t* ox, const uint64_t
     if (ow && cudaMemcpyAsync(o.ow, ow, (size_t)m * 8, cudaMemcpyHostToDevice, h->stream) !=
                   cudaSuccess)
         return cuda_fail(h);
+    if (launch_materialize(h->s, h->stream) != cudaSuccess) return cuda_fail(h);
     EventPair* ev = prof_begin(h, 3);
     cudaError_t e = launch_expect(h->s, o.ox, o.oz, ow ? o.ow : nullptr, m, o.tsize, o.tab,
                                   o.first, o.vals, o.out, h->stream);

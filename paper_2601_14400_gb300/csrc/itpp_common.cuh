@@ -85,6 +85,15 @@ struct DevCtl {
     unsigned long long sel_tie_k;    // rank still to place in the tie select
     int sel_tie_state;               // 0 running, 1 key known, 2 unique prefix found
     int sel_tie_pass;
+    unsigned long long sel_cand_n;   // candidates gathered after the first digit
+    // deferred top-M compaction: the state buffer holds pend_n terms of which
+    // the select's kept set (sel_prefix / tie key) is the state; the next
+    // gate's scatter or an explicit materialisation applies it
+    int pend;
+    int pend_all_ties;
+    unsigned long long pend_n;
+    unsigned long long pend_T;
+    uint64_t pend_tie_key[4];
     uint64_t sel_tie_key[4];         // largest kept tie key (x..., z...)
     unsigned long long sel_hist[kSelBins];
     unsigned long long tie_hist[kTieBins];
@@ -158,6 +167,15 @@ __device__ __forceinline__ bool key_is_zero(const PKey<W>& k) {
     return a == 0;
 }
 
+// Whether k * Q (Q the gate's string) is the identity, i.e. k == Q.
+template <int W>
+__device__ __forceinline__ bool key_is_zero_xor(const PKey<W>& k, const GateArg<W>& g) {
+    uint64_t a = 0;
+#pragma unroll
+    for (int w = 0; w < W; ++w) a |= (k.x[w] ^ g.qx[w]) | (k.z[w] ^ g.qz[w]);
+    return a == 0;
+}
+
 template <int W>
 __device__ __forceinline__ bool key_eq(const PKey<W>& a, const PKey<W>& b) {
     uint64_t d = 0;
@@ -179,27 +197,38 @@ __device__ __forceinline__ bool key_less(const PKey<W>& a, const PKey<W>& b) {
 }
 
 // ---------------------------------------------------------------------------
-// Hashing of keys for the merge table (murmur3 finaliser, chained so that
-// flips of the same bit in x and z do not cancel).
+// Hashing of keys: MurmurHash3 (x86, 32-bit) over the 4W 32-bit halves of
+// the key.  Only 32-bit multiplies: on GB300 the 64-bit integer multiply of
+// a 64-bit mixer competes with the FP64 arithmetic for the same slow pipe.
 // ---------------------------------------------------------------------------
-__device__ __forceinline__ uint64_t fmix64(uint64_t k) {
-    k ^= k >> 33;
-    k *= 0xff51afd7ed558ccdULL;
-    k ^= k >> 33;
-    k *= 0xc4ceb9fe1a85ec53ULL;
-    k ^= k >> 33;
-    return k;
+__device__ __forceinline__ uint32_t rotl32(uint32_t x, int r) { return (x << r) | (x >> (32 - r)); }
+
+__device__ __forceinline__ uint32_t murmur_mix(uint32_t h, uint32_t k) {
+    k *= 0xcc9e2d51u;
+    k = rotl32(k, 15);
+    k *= 0x1b873593u;
+    h ^= k;
+    h = rotl32(h, 13);
+    return h * 5u + 0xe6546b64u;
 }
 
 template <int W>
 __device__ __forceinline__ uint64_t key_hash(const PKey<W>& k) {
-    uint64_t h = 0x9E3779B97F4A7C15ULL;
+    uint32_t h = 0x9747b28cu;
 #pragma unroll
     for (int w = 0; w < W; ++w) {
-        h = fmix64(h ^ k.z[w]);
-        h = fmix64(h ^ k.x[w]);
+        h = murmur_mix(h, (uint32_t)k.x[w]);
+        h = murmur_mix(h, (uint32_t)(k.x[w] >> 32));
+        h = murmur_mix(h, (uint32_t)k.z[w]);
+        h = murmur_mix(h, (uint32_t)(k.z[w] >> 32));
     }
-    return h;
+    h ^= 16u * W;
+    h ^= h >> 16;
+    h *= 0x85ebca6bu;
+    h ^= h >> 13;
+    h *= 0xc2b2ae35u;
+    h ^= h >> 16;
+    return (uint64_t)h;
 }
 
 // Slots of the table used when the input holds n terms (load <= load_pct%).

@@ -102,6 +102,20 @@ __device__ __forceinline__ bool table_insert(Slot<W>* table, uint64_t mask, unsi
     return false;
 }
 
+// Partner lookup in the global merge table.
+template <int W>
+struct GlobalLookup {
+    const Slot<W>* table;
+    uint64_t mask;
+    unsigned gen;
+    int probe_limit;
+    DevCtl* ctl;
+    int* probes;
+    __device__ __forceinline__ bool find(const PKey<W>& P, double* c, uint32_t* idx) const {
+        return table_find(table, mask, gen, P, c, probe_limit, ctl, probes, idx);
+    }
+};
+
 // One input term of the table build: commuting terms are inserted.
 template <int W>
 __device__ __forceinline__ void insert_one(const PKey<W>* __restrict__ kin,
@@ -129,17 +143,15 @@ struct StepMaps {
     unsigned long long* id_pos;   // output position of the identity
 };
 
-template <int W, int BLOCK, int IPT, bool REC = false>
+template <int W, int BLOCK, int IPT, bool REC = false, class Lookup = GlobalLookup<W>>
 __device__ __forceinline__ void gate_tile(uint64_t t, uint64_t n,
                                           const PKey<W>* __restrict__ kin,
                                           const double* __restrict__ cin,
                                           PKey<W>* __restrict__ kout, double* __restrict__ cout,
-                                          DevCtl* ctl, int cur,
-                                          const Slot<W>* __restrict__ table, uint64_t mask,
-                                          unsigned gen, const GateArg<W>& g, double rnorm,
+                                          DevCtl* ctl, int cur, const Lookup& lk,
+                                          const GateArg<W>& g, double rnorm,
                                           unsigned long long dbits, uint64_t cap_out,
-                                          int probe_limit, uint32_t* s_scan,
-                                          unsigned long long* s_base, int* probes,
+                                          uint32_t* s_scan, unsigned long long* s_base,
                                           StepMaps maps = StepMaps{nullptr, nullptr, nullptr,
                                                                    nullptr}) {
     constexpr uint64_t TILE = (uint64_t)BLOCK * IPT;
@@ -151,36 +163,43 @@ __device__ __forceinline__ void gate_tile(uint64_t t, uint64_t n,
 #pragma unroll
     for (int j = 0; j < IPT; ++j) {
         const uint64_t i = i0 + j;
-        va[j] = 0.0;
-        vb[j] = 0.0;
         psrc[j] = -1;
+        double raw = 0.0, cp_raw = 0.0;
+        bool comm = false, found = false, neg = false;
 #pragma unroll
         for (int w = 0; w < W; ++w) { K[j].x[w] = 0; K[j].z[w] = 0; }
+        // integer phase: commutation, the partner's lookup, the product's sign
         if (i < n) {
             K[j] = load_key_stream(kin + i);
-            // normalise on load: the previous gate's trace rescaling
-            const double c = normalised(__ldcs(cin + i), rnorm, key_is_zero(K[j]));
-            bool keep_b = false;
-            if (!commutes(K[j], g)) {
-                va[j] = c;                                       // {P,Q} = 0: unchanged
-            } else {
-                const double m = product_negative(K[j], g) ? -g.msh : g.msh;
-                const PKey<W> P = key_xor(K[j], g);
-                double cp_raw;
+            raw = __ldcs(cin + i);
+            comm = commutes(K[j], g);
+            if (comm) {
+                neg = product_negative(K[j], g);
                 uint32_t pidx = 0;
-                if (table_find(table, mask, gen, P, &cp_raw, probe_limit, ctl, probes,
-                               REC ? &pidx : nullptr)) {
-                    if (REC) psrc[j] = (int)pidx;
-                    const double cp = normalised(cp_raw, rnorm, key_is_zero(P));
-                    va[j] = __dadd_rn(__dmul_rn(c, g.ch), __dmul_rn(cp, m));
-                } else {
-                    va[j] = __dmul_rn(c, g.ch);                  // cosh(theta) P
-                    vb[j] = __dmul_rn(c, m);                     // -sinh(theta) s (Q.P)
-                    keep_b = above(vb[j], dbits);
-                }
+                found = lk.find(key_xor(K[j], g), &cp_raw, REC ? &pidx : nullptr);
+                if (REC && found) psrc[j] = (int)pidx;
             }
-            bool keep_a = above(va[j], dbits);
-            if (key_is_zero(K[j])) {
+        }
+        // floating-point phase, the same operations on every lane (no
+        // divergent double-precision issue); the branch's result is selected
+        // afterwards.  Normalise on load (the previous gate's trace
+        // rescaling), the identity being exactly 1.
+        const bool id = key_is_zero(K[j]);
+        const bool pid = comm && key_is_zero_xor(K[j], g);
+        const double c = id ? 1.0 : __dmul_rn(raw, rnorm);
+        const double cpn = pid ? 1.0 : __dmul_rn(cp_raw, rnorm);
+        // s (-sinh): the sign flip is an integer XOR of the sign bit
+        const double m = __longlong_as_double(
+            __double_as_longlong(g.msh) ^ (neg ? (long long)0x8000000000000000ULL : 0LL));
+        const double a1 = __dmul_rn(c, g.ch);           // cosh(theta) P
+        const double b1 = __dmul_rn(c, m);              // -sinh(theta) s (Q.P), no partner
+        const double sum = __dadd_rn(a1, __dmul_rn(cpn, m));   // partner QP present
+        va[j] = !comm ? c : (found ? sum : a1);         // {P,Q} = 0: unchanged
+        vb[j] = b1;
+        bool keep_b = comm && !found && above(b1, dbits);
+        bool keep_a = above(va[j], dbits);
+        if (i < n) {
+            if (id) {
                 // the identity: its merged coefficient is the new trace
                 ctl->norm[cur ^ 1] = va[j];
                 if (!keep_a) set_status(ctl, ST_TRACE_ZERO, 1);
@@ -228,6 +247,7 @@ __device__ __forceinline__ void gate_tile(uint64_t t, uint64_t n,
 // table generation, statistics and the term bound.  Returns 1 when the top-M
 // select must run.
 __device__ __forceinline__ int post_one(DevCtl* ctl, uint64_t cap_M, int cap_policy) {
+    ctl->pend = 0;   // a deferred select was applied by this gate's scatter
     const int cur = ctl->cur, nxt = cur ^ 1;
     const unsigned long long n_in = ctl->count[cur], n_out = ctl->count[nxt];
     ctl->cur = nxt;
@@ -252,6 +272,7 @@ __device__ __forceinline__ int post_one(DevCtl* ctl, uint64_t cap_M, int cap_pol
             ctl->sel_tie_k = 0;
             ctl->sel_tie_state = 0;
             ctl->sel_tie_pass = 0;
+            ctl->sel_cand_n = 0;
             for (int w = 0; w < 4; ++w) ctl->sel_tie_key[w] = 0;
             ctl->stat_cap += 1;
         }

@@ -22,6 +22,14 @@ struct DeviceState {
     // launch shape
     int num_sms = 1;
     int block = 256, ipt = 2, load_pct = 50, probe_limit = 4096;
+    // partitioned merge (itpp_part.cu): scatter buffer and cursors
+    void* part_keys = nullptr;        // PKey<W>[part_cap]
+    double* part_coef = nullptr;      // double[part_cap]
+    unsigned int* part_cursor = nullptr;   // [part_max]
+    uint64_t part_cap = 0;
+    uint32_t part_max = 0;
+    // top-M select leaves its kept set as a predicate for the next scatter
+    bool merge_deferred = false;
 };
 
 // Per-gate host constants (computed once in itpp_create).
@@ -36,12 +44,19 @@ struct HostGate {
 cudaError_t launch_gate_insert(const DeviceState& s, const HostGate& g, cudaStream_t st);
 cudaError_t launch_gate_main(const DeviceState& s, const HostGate& g, cudaStream_t st);
 cudaError_t launch_gate_post(const DeviceState& s, cudaStream_t st);
+// Partitioned merge: scatter by pair key, then one shared-memory table per
+// partition (the default merge of a single propagation).
+cudaError_t launch_part_scatter(const DeviceState& s, const HostGate& g, cudaStream_t st);
+cudaError_t launch_part_merge(const DeviceState& s, const HostGate& g, cudaStream_t st);
+uint32_t partition_max(int W, uint64_t cap_M);
 // Top-M select and compaction (no-ops on the device when the bound holds).
 cudaError_t launch_cap(const DeviceState& s, cudaStream_t st);
 int cap_launches(const DeviceState& s);
 // The select part only (threshold and tie key in the control block, no
 // compaction): used where the kept set is compacted elsewhere.
 cudaError_t launch_cap_select(const DeviceState& s, cudaStream_t st);
+// Apply a deferred top-M select (compaction); a no-op when none is pending.
+cudaError_t launch_materialize(const DeviceState& s, cudaStream_t st);
 // Sort-based merge path (children buffer, radix sort, segmented reduce).
 cudaError_t launch_gate_sorted(const DeviceState& s, const HostGate& g, void* scratch,
                                uint64_t scratch_bytes, cudaStream_t st);

@@ -244,10 +244,23 @@ def test_create_validation():
 def test_launch_shapes_give_identical_states(block, ipt, load):
     H = wl.tfim_1d(12, 1.0, 1.0, periodic=True)
     g, o = _pair(H, 0.05, 1e-7, cap_M=1 << 18, block_threads=block, items_per_thread=ipt,
-                 table_load_pct=load)
+                 table_load_pct=load, merge_path=2)
     g.apply_trotter_layer(3)
     o.apply_layers(3)
     assert_same_state(g.terms(), o.terms(), f"block={block} ipt={ipt} load={load}")
+
+
+@pytest.mark.parametrize("n,W_delta", [(64, 1e-4), (100, 2e-4)])
+def test_merge_paths_identical(n, W_delta):
+    # partitioned shared-memory merge vs one global table, many partitions
+    H = wl.tfim_1d(n, 1.0, 1.0, periodic=True)
+    a = itpp.Propagator(H.n, H.gate_x, H.gate_z, H.alpha, 0.05, W_delta, 1 << 22, merge_path=0)
+    b = itpp.Propagator(H.n, H.gate_x, H.gate_z, H.alpha, 0.05, W_delta, 1 << 22, merge_path=2)
+    a.apply_trotter_layer(2)
+    b.apply_trotter_layer(2)
+    assert a.count() > 20000
+    from tests._compare import sort_terms
+    assert_same_state(a.terms(), sort_terms(*b.terms()), f"n={n}")
 
 
 # ---------------------------------------------------------------------------
