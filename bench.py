@@ -401,11 +401,13 @@ def main():
     torch.cuda.synchronize()
     ev0 = torch.cuda.Event(enable_timing=True)
     ev1 = torch.cuda.Event(enable_timing=True)
+    torch.cuda.profiler.start()   # ncu --profile-from-start off: timed launches only
     ev0.record(stream)
     g.apply_trotter_layer(args.steps)
     ev1.record(stream)
     g.synchronize()
     torch.cuda.synchronize()
+    torch.cuda.profiler.stop()
     barrier(world)
     clk = clocks.stop()
     ms = ev0.elapsed_time(ev1)

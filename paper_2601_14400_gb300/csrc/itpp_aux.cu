@@ -371,7 +371,7 @@ k_trunc(BufsA<W> B, DevCtl* ctl, double delta) {
         if (i < n) {
             K = load_key_stream(B.k[cur] + i);
             c = normalised(__ldcs(B.c[cur] + i), rnorm, key_is_zero(K));
-            keep = fabs(c) > delta;
+            keep = above(c, (unsigned long long)__double_as_longlong(delta));
             if (key_is_zero(K) && !keep) {
                 set_status(ctl, ST_TRACE_ZERO, 20);
                 keep = true;

@@ -165,7 +165,7 @@ itpp_status itpp_batch_create(int B, const int* n, const int* n_gates, const uin
     s.cap_M = p->cap_M;
     s.buf_cap = 2 * p->cap_M;
     s.cap_policy = p->cap_policy;
-    s.delta = p->delta;
+    s.delta = p->delta + 0.0;   // -0 becomes +0 (the threshold compares bit patterns)
     s.load_pct = p->table_load_pct ? p->table_load_pct : 50;
     if (s.load_pct < 10 || s.load_pct > 75) { free_batch(h); delete h; return ITPP_ERR_ARG; }
     const int load_for_size = s.load_pct < 50 ? s.load_pct : 50;

@@ -255,12 +255,12 @@ itpp_status itpp_create(int n, const uint64_t* gate_x, const uint64_t* gate_z,
     s.cap_M = p->cap_M;
     s.buf_cap = 2 * p->cap_M;
     s.cap_policy = p->cap_policy;
-    s.delta = p->delta;
+    s.delta = p->delta + 0.0;   // -0 becomes +0 (the threshold compares bit patterns)
     s.load_pct = p->table_load_pct ? p->table_load_pct : 50;
-    // defaults from the block-shape sweep: 512 x 1 for the partitioned merge,
-    // 256 x 2 for the global-table merge
+    // defaults: 512 x 2 for the partitioned merge (a whole partition in
+    // registers), 256 x 2 for the global-table merge
     s.block = p->block_threads ? p->block_threads : (p->merge_path == 0 ? 512 : 256);
-    s.ipt = p->items_per_thread ? p->items_per_thread : (p->merge_path == 0 ? 1 : 2);
+    s.ipt = p->items_per_thread ? p->items_per_thread : 2;
     s.merge_deferred = p->merge_path == 0;
     s.probe_limit = 4096;
     const int load_for_size = s.load_pct < 50 ? s.load_pct : 50;
@@ -359,7 +359,7 @@ itpp_status itpp_truncate(itpp_handle h, double delta) {
     if (!h || !(delta >= 0.0) || !std::isfinite(delta)) return ITPP_ERR_ARG;
     if (h->sticky) return h->sticky;
     if (launch_materialize(h->s, h->stream) != cudaSuccess) return cuda_fail(h);
-    return launch_truncate(h->s, delta, h->stream) == cudaSuccess ? ITPP_OK : cuda_fail(h);
+    return launch_truncate(h->s, delta + 0.0, h->stream) == cudaSuccess ? ITPP_OK : cuda_fail(h);
 }
 
 itpp_status itpp_synchronize(itpp_handle h) {

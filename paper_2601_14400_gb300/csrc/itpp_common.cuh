@@ -106,12 +106,21 @@ __device__ __forceinline__ uint64_t live_count(const DevCtl* ctl, int b) {
     return n < ctl->buf_cap ? n : ctl->buf_cap;
 }
 
+// The 63-bit magnitude pattern of a double.  The mask is applied in inline
+// PTX so that the compiler does not turn it into a floating-point |x|, which
+// would run on the (slow, shared) double-precision pipe.
+__device__ __forceinline__ unsigned long long abs_pattern(double c) {
+    unsigned long long r;
+    asm("and.b64 %0, %1, 0x7fffffffffffffff;" : "=l"(r) : "l"(__double_as_longlong(c)));
+    return r;
+}
+
 // |c| > delta for delta >= 0, decided on the bit patterns: for non-negative
 // doubles the unsigned order of the patterns is the numeric order, so this is
 // exact (NaN patterns exceed +inf and count as kept, where fabs(c) > delta
 // would drop them; the propagation produces no NaN from finite inputs).
 __device__ __forceinline__ bool above(double c, unsigned long long delta_bits) {
-    return ((unsigned long long)__double_as_longlong(c) & 0x7fffffffffffffffULL) > delta_bits;
+    return abs_pattern(c) > delta_bits;
 }
 
 // Normalised value of a stored coefficient.

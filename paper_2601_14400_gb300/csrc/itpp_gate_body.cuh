@@ -292,7 +292,7 @@ __device__ __forceinline__ int post_one(DevCtl* ctl, uint64_t cap_M, int cap_pol
 // the kept set is "the cap_M largest |c|, ties by ascending key".
 // ---------------------------------------------------------------------------
 __device__ __forceinline__ unsigned long long abs_bits(double c) {
-    return (unsigned long long)__double_as_longlong(c) & 0x7fffffffffffffffULL;
+    return abs_pattern(c);
 }
 
 // Block-wide 64-bit inclusive scan of one value per thread (1024 threads).

@@ -153,7 +153,7 @@ extern "C" itpp_status itpp_gate_apply_noalloc(
     s.cap_M = 0;
     s.buf_cap = out_capacity > n_in ? out_capacity : n_in;
     s.cap_policy = 0;
-    s.delta = delta;
+    s.delta = delta + 0.0;   // -0 becomes +0 (the threshold compares bit patterns)
     int dev = 0, sms = 1;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);

@@ -68,27 +68,6 @@ __device__ __forceinline__ uint32_t part_of(const PKey<W>& K, const GateArg<W>& 
     return (uint32_t)((h * (uint64_t)P) >> 32);
 }
 
-template <int W>
-struct SmemLookup {
-    const PKey<W>* keys;
-    const double* c;
-    const uint32_t* tag;
-    __device__ __forceinline__ bool find(const PKey<W>& P, double* out, uint32_t* idx) const {
-        constexpr uint32_t mask = PartGeom<W>::kSlots - 1;
-        uint32_t h = (uint32_t)key_hash(P) & mask;
-        for (int p = 0; p < PartGeom<W>::kSlots; ++p) {
-            if (tag[h] == 0u) return false;
-            if (key_eq(keys[h], P)) {
-                *out = c[h];
-                if (idx) *idx = 0;
-                return true;
-            }
-            h = (h + 1) & mask;
-        }
-        return false;
-    }
-};
-
 }  // namespace
 
 // Scatter the current state into partitions of the gate's pair key.
@@ -136,7 +115,94 @@ k_part_scatter(Bufs<W> B, DevCtl* ctl, PKey<W>* pk, double* pc, unsigned int* cu
     }
 }
 
-// One partition at a time per CTA: shared-memory table, then the tile body.
+// Per-item quantities of the gate on one stored term (Eq. for the commuting
+// branch: cosh(theta) P and -sinh(theta) s QP).  c is the normalised input
+// coefficient, b = c * (-sinh(theta) s) the child it sends to its partner QP.
+// For a commuting pair {K, QK} the product sign s is the same seen from both
+// members (Q K = s QK implies Q QK = s K), so the partner's incoming addend
+// is exactly the b its own thread computes: each term multiplies once by
+// rnorm, once by ch and once by msh, and adds its partner's b.
+template <int W>
+struct PartItem {
+    PKey<W> K;
+    double c, b;
+    bool comm, live;
+};
+
+template <int W>
+__device__ __forceinline__ PartItem<W> part_item(const PKey<W>* kp, const double* cp, uint64_t i,
+                                                 uint64_t np, const GateArg<W>& g, double rnorm) {
+    PartItem<W> it;
+    double raw = 0.0;
+    bool neg = false;
+#pragma unroll
+    for (int w = 0; w < W; ++w) { it.K.x[w] = 0; it.K.z[w] = 0; }
+    it.live = i < np;
+    it.comm = false;
+    if (it.live) {
+        it.K = load_key_stream(kp + i);
+        raw = __ldcs(cp + i);
+        it.comm = commutes(it.K, g);
+        neg = it.comm && product_negative(it.K, g);
+    }
+    // the same double-precision operations on every lane; the identity's
+    // normalised value is exactly 1
+    it.c = key_is_zero(it.K) ? 1.0 : __dmul_rn(raw, rnorm);
+    const double m = __longlong_as_double(
+        __double_as_longlong(g.msh) ^ (neg ? (long long)0x8000000000000000ULL : 0LL));
+    it.b = __dmul_rn(it.c, m);
+    return it;
+}
+
+// Shared-memory table of one partition: commuting keys and their b.
+template <int W>
+__device__ __forceinline__ bool part_insert(const PartItem<W>& it, PKey<W>* t_keys, double* t_b,
+                                            uint32_t* t_tag) {
+    constexpr uint32_t S = PartGeom<W>::kSlots;
+    uint32_t h = (uint32_t)key_hash(it.K) & (S - 1);
+    for (uint32_t q = 0; q < S; ++q) {
+        if (atomicCAS(t_tag + h, 0u, 1u) == 0u) {
+            t_keys[h] = it.K;
+            t_b[h] = it.b;
+            return true;
+        }
+        h = (h + 1) & (S - 1);
+    }
+    return false;
+}
+
+template <int W>
+__device__ __forceinline__ bool part_find(const PKey<W>& P, const PKey<W>* t_keys,
+                                          const double* t_b, const uint32_t* t_tag, double* out) {
+    constexpr uint32_t S = PartGeom<W>::kSlots;
+    uint32_t h = (uint32_t)key_hash(P) & (S - 1);
+    for (uint32_t q = 0; q < S; ++q) {
+        if (t_tag[h] == 0u) return false;
+        if (key_eq(t_keys[h], P)) { *out = t_b[h]; return true; }
+        h = (h + 1) & (S - 1);
+    }
+    return false;
+}
+
+// Branch, merge and truncation of one item against the complete table:
+// va (self child, merged) and whether the QP child is emitted.
+template <int W>
+__device__ __forceinline__ void part_children(const PartItem<W>& it, const GateArg<W>& g,
+                                              const PKey<W>* t_keys, const double* t_b,
+                                              const uint32_t* t_tag, double* va, bool* emit_b) {
+    double pb = 0.0;
+    bool found = false;
+    if (it.comm) found = part_find(key_xor(it.K, g), t_keys, t_b, t_tag, &pb);
+    const double a1 = __dmul_rn(it.c, g.ch);          // cosh(theta) P
+    const double sum = __dadd_rn(a1, pb);             // + the partner's child
+    *va = !it.comm ? it.c : (found ? sum : a1);       // {P,Q} = 0: unchanged
+    *emit_b = it.comm && !found;
+}
+
+// One partition at a time per CTA: the partition's items stay in registers
+// (BLOCK x IPT of them; a longer partition reloads the rest), the commuting
+// ones publish (key, b) in a shared-memory table, then every item merges
+// with its partner's b and the kept children are written out.
 template <int W, int kPBlock, int kPIpt>
 __global__ void __launch_bounds__(kPBlock)
 k_gate_part(const PKey<W>* __restrict__ pk, const double* __restrict__ pc,
@@ -144,9 +210,10 @@ k_gate_part(const PKey<W>* __restrict__ pk, const double* __restrict__ pc,
             uint64_t pbuf_cap, uint32_t p_max, GateArg<W> g, double delta, uint64_t cap_out) {
     extern __shared__ __align__(16) unsigned char smem[];
     constexpr int S = PartGeom<W>::kSlots;
+    constexpr uint64_t CHUNK = (uint64_t)kPBlock * kPIpt;
     PKey<W>* t_keys = reinterpret_cast<PKey<W>*>(smem);
-    double* t_c = reinterpret_cast<double*>(t_keys + S);
-    uint32_t* t_tag = reinterpret_cast<uint32_t*>(t_c + S);
+    double* t_b = reinterpret_cast<double*>(t_keys + S);
+    uint32_t* t_tag = reinterpret_cast<uint32_t*>(t_b + S);
     __shared__ uint32_t s_scan[kPBlock / 32];
     __shared__ unsigned long long s_base;
     if (ctl->status) return;
@@ -155,8 +222,8 @@ k_gate_part(const PKey<W>* __restrict__ pk, const double* __restrict__ pc,
     const PartPlan pl = part_plan(n, pbuf_cap, p_max, PartGeom<W>::kTarget);
     const double rnorm = ctl->rnorm[cur];
     const unsigned long long dbits = (unsigned long long)__double_as_longlong(delta);
-    const SmemLookup<W> lk{t_keys, t_c, t_tag};
-    constexpr uint64_t TILE = (uint64_t)kPBlock * kPIpt;
+    PKey<W>* __restrict__ kout = B.k[cur ^ 1];
+    double* __restrict__ cout = B.c[cur ^ 1];
     for (uint32_t p = blockIdx.x; p < pl.P; p += gridDim.x) {
         uint64_t np = cursor[p];
         if (np > pl.R) np = pl.R;
@@ -174,31 +241,68 @@ k_gate_part(const PKey<W>* __restrict__ pk, const double* __restrict__ pc,
             for (uint64_t b = (uint64_t)threadIdx.x * 128; b < nn * sizeof(double); b += 128 * kPBlock)
                 asm volatile("prefetch.global.L2 [%0];" :: "l"(nc + b));
         }
-        for (int s = threadIdx.x; s < S; s += kPBlock) t_tag[s] = 0u;
+        for (int s2 = threadIdx.x; s2 < S; s2 += kPBlock) t_tag[s2] = 0u;
         __syncthreads();
-        // the partition's commuting terms into the shared table
-        for (uint64_t i = threadIdx.x; i < np; i += kPBlock) {
-            const PKey<W> K = kp[i];
-            if (!commutes(K, g)) continue;
-            uint32_t h = (uint32_t)key_hash(K) & (S - 1);
-            int q = 0;
-            for (; q < S; ++q) {
-                if (atomicCAS(t_tag + h, 0u, 1u) == 0u) {
-                    t_keys[h] = K;
-                    t_c[h] = cp[i];
-                    break;
-                }
-                h = (h + 1) & (S - 1);
-            }
-            if (q == S) set_status(ctl, ST_CAPACITY, 41);
+        // items j*BLOCK + tid (coalesced), kept in registers
+        PartItem<W> it[kPIpt];
+        bool ok = true;
+#pragma unroll
+        for (int j = 0; j < kPIpt; ++j) {
+            it[j] = part_item(kp, cp, (uint64_t)j * kPBlock + threadIdx.x, np, g, rnorm);
+            if (it[j].comm) ok &= part_insert(it[j], t_keys, t_b, t_tag);
         }
+        for (uint64_t i = CHUNK + threadIdx.x; i < np; i += kPBlock) {
+            const PartItem<W> x = part_item(kp, cp, i, np, g, rnorm);
+            if (x.comm) ok &= part_insert(x, t_keys, t_b, t_tag);
+        }
+        if (!ok) set_status(ctl, ST_CAPACITY, 41);
         __syncthreads();
-        const uint64_t tiles = (np + TILE - 1) / TILE;
-        for (uint64_t t = 0; t < tiles; ++t) {
-            gate_tile<W, kPBlock, kPIpt, false, SmemLookup<W>>(t, np, kp, cp, B.k[cur ^ 1],
-                                                              B.c[cur ^ 1], ctl, cur, lk, g,
-                                                              rnorm, dbits, cap_out, s_scan,
-                                                              &s_base);
+        // the chunk held in registers, then (rarely) the rest of a long partition
+        for (uint64_t c0 = 0; c0 < np; c0 += CHUNK) {
+            double va[kPIpt];
+            bool eb[kPIpt];
+            uint32_t flags = 0;
+#pragma unroll
+            for (int j = 0; j < kPIpt; ++j) {
+                if (c0) it[j] = part_item(kp, cp, c0 + (uint64_t)j * kPBlock + threadIdx.x, np, g, rnorm);
+                part_children(it[j], g, t_keys, t_b, t_tag, &va[j], &eb[j]);
+                bool keep_a = above(va[j], dbits);
+                const bool keep_b = eb[j] && above(it[j].b, dbits);
+                if (it[j].live) {
+                    if (key_is_zero(it[j].K)) {
+                        // the identity: its merged coefficient is the new trace
+                        ctl->norm[cur ^ 1] = va[j];
+                        if (!keep_a) set_status(ctl, ST_TRACE_ZERO, 1);
+                        keep_a = true;
+                    }
+                    flags |= (keep_a ? 1u : 0u) << (2 * j);
+                    flags |= (keep_b ? 1u : 0u) << (2 * j + 1);
+                }
+            }
+            uint32_t tot;
+            const uint32_t off = block_exclusive_scan<kPBlock>(__popc(flags), &tot, s_scan);
+            if (threadIdx.x == 0)
+                s_base = tot ? atomicAdd(&ctl->count[cur ^ 1], (unsigned long long)tot) : 0ULL;
+            __syncthreads();
+            const unsigned long long base = s_base;
+            if (base + tot > cap_out) {
+                if (threadIdx.x == 0) set_status(ctl, ST_CAPACITY, 2);
+                return;
+            }
+            uint64_t pos = base + off;
+#pragma unroll
+            for (int j = 0; j < kPIpt; ++j) {
+                if ((flags >> (2 * j)) & 1u) {
+                    store_key_stream(kout + pos, it[j].K);
+                    __stcs(cout + pos, va[j]);
+                    ++pos;
+                }
+                if ((flags >> (2 * j + 1)) & 1u) {
+                    store_key_stream(kout + pos, key_xor(it[j].K, g));
+                    __stcs(cout + pos, it[j].b);
+                    ++pos;
+                }
+            }
             __syncthreads();
         }
     }

@@ -147,6 +147,17 @@ def test_identity_only_and_delta_zero():
     assert_same_state(g.terms(), o.terms(), "delta=0")
 
 
+def test_negative_zero_delta_is_zero():
+    # the threshold is compared on bit patterns: -0.0 must act as +0.0
+    H = wl.tfim_1d(5, 1.0, 0.7)
+    g, o = _pair(H, 0.1, -0.0)
+    g.apply_trotter_layer(3)
+    o.apply_layers(3)
+    assert_same_state(g.terms(), o.terms(), "delta=-0")
+    g.truncate(-0.0)
+    assert_same_state(g.terms(), o.terms(), "truncate(-0)")
+
+
 def test_everything_truncated_but_identity():
     H = wl.tfim_1d(5, 1.0, 1.0)
     g, o = _pair(H, 0.05, 0.5)
