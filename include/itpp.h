@@ -78,6 +78,11 @@ typedef struct {
      * 0: partitioned merge (default): the state is scattered into hash
      *    partitions of the pair key {K, Q.K}, and each partition is merged
      *    through an open-addressing table in shared memory.
+     * 1: sort fallback: the commuting terms' children are radix-sorted on
+     *    the whole key (8-bit digits, digits above bit n skipped) and runs of
+     *    equal keys are summed by a segmented reduce; anticommuting terms,
+     *    which never share a string with another child, bypass the sort.
+     *    Needs a scratch of about 2 * (2 cap_M) children.
      * 2: one open-addressing table in global memory for the whole state. */
     int merge_path;
     /* Tuning (0 = library default or the autotuned value):

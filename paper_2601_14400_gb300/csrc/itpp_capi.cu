@@ -119,6 +119,11 @@ itpp_status launch_one_gate(itpp_ctx* h, int k) {
             e = launch_part_merge(h->s, g, h->stream);
             prof_end(h, ev1);
         }
+    } else if (h->p.merge_path == 1) {
+        EventPair* ev1 = prof_begin(h, 1);
+        e = launch_gate_sorted(h->s, g, h->sort_mem, h->sort_bytes, h->stream);
+        prof_end(h, ev1);
+        h->launches += sorted_launches(h->s.n, h->s.W) - 2;
     } else {
         EventPair* ev0 = prof_begin(h, 0);
         e = launch_gate_insert(h->s, g, h->stream);
@@ -221,7 +226,7 @@ itpp_status itpp_create(int n, const uint64_t* gate_x, const uint64_t* gate_z,
     if (!std::isfinite(dtau) || !(p->delta >= 0.0) || !std::isfinite(p->delta)) return ITPP_ERR_ARG;
     if (p->cap_M < 1 || p->cap_M > (1ULL << 31)) return ITPP_ERR_ARG;
     if (p->cap_policy != 0 && p->cap_policy != 1) return ITPP_ERR_ARG;
-    if (p->merge_path != 0 && p->merge_path != 2) return ITPP_ERR_ARG;
+    if (p->merge_path < 0 || p->merge_path > 2) return ITPP_ERR_ARG;
     if (p->table_load_pct != 0 && (p->table_load_pct < 10 || p->table_load_pct > 75))
         return ITPP_ERR_ARG;
     if (p->block_threads != 0 && p->block_threads != 128 && p->block_threads != 256 &&
@@ -300,6 +305,10 @@ itpp_status itpp_create(int n, const uint64_t* gate_x, const uint64_t* gate_z,
         ok &= ok && cudaMalloc(reinterpret_cast<void**>(&s.part_coef), s.part_cap * 8) == cudaSuccess;
         ok &= ok && cudaMalloc(reinterpret_cast<void**>(&s.part_cursor),
                                (size_t)s.part_max * sizeof(unsigned int)) == cudaSuccess;
+    }
+    if (ok && p->merge_path == 1) {
+        h->sort_bytes = sorted_scratch_bytes(W, s.buf_cap);
+        ok &= cudaMalloc(&h->sort_mem, h->sort_bytes) == cudaSuccess;
     }
     if (!ok) {
         cudaGetLastError();

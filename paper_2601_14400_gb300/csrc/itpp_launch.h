@@ -61,6 +61,7 @@ cudaError_t launch_materialize(const DeviceState& s, cudaStream_t st);
 cudaError_t launch_gate_sorted(const DeviceState& s, const HostGate& g, void* scratch,
                                uint64_t scratch_bytes, cudaStream_t st);
 uint64_t sorted_scratch_bytes(int W, uint64_t buf_cap);
+int sorted_launches(int n, int W);
 
 // Expectation: obs table build, state scan, reduction.  d_tab holds
 // tsize ints, d_first m ints, d_vals m doubles.
