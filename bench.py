@@ -37,10 +37,21 @@ import workloads as wl  # noqa: E402
 
 METRIC = "Pauli terms/s per Trotter gate"
 UNIT = "terms/s"
-KERNEL_NAMES = {0: "k_gate_insert (merge-table build)",
-                1: "k_gate_main (branch-emit-merge-truncate)",
-                2: "top-M select chain (k_cap_*, k_tie_*)",
-                3: "expectation (k_obs_*)"}
+# Profiling kinds of the library (itpp_profile_read) per merge path.
+KERNEL_NAMES = {
+    0: {0: "k_part_scatter (scatter by pair key)",
+        1: "k_gate_part (partition merge: branch-emit-merge-truncate)",
+        2: "top-M select chain (k_cap_*, k_cand_*, k_tie_*)",
+        3: "expectation (k_obs_*)"},
+    1: {0: "(unused)",
+        1: "sorted merge (expand, radix passes, segmented reduce)",
+        2: "top-M select chain (k_cap_*, k_tie_*)",
+        3: "expectation (k_obs_*)"},
+    2: {0: "k_gate_insert (global merge-table build)",
+        1: "k_gate_main (branch-emit-merge-truncate)",
+        2: "top-M select chain (k_cap_*, k_tie_*)",
+        3: "expectation (k_obs_*)"},
+}
 
 
 def parse():
@@ -430,7 +441,10 @@ def main():
     # algorithmic bytes of one elementary gate: every input term read once,
     # every kept term written once
     b_alg_gate = (terms_in + terms_out) * term_bytes / max(gates, 1)
-    if dom == 0:
+    if dom == 0 and args.merge_path == 0:
+        # the scatter reads every input term and writes it to its partition
+        b_alg_dom = 2 * terms_in * term_bytes / max(gates, 1)
+    elif dom == 0:
         # the table build reads each input key once (coefficients of the
         # commuting terms are not counted)
         b_alg_dom = terms_in * (16 * W) / max(gates, 1)
@@ -493,7 +507,7 @@ def main():
                        "terms_at_start": st0["count"],
                        "l2": "state larger than L2 (no flush)",
                        "parallelism": f"replicas x{world}"},
-            "roofline": {"bound": "hbm", "kernel": KERNEL_NAMES[dom],
+            "roofline": {"bound": "hbm", "kernel": KERNEL_NAMES[args.merge_path][dom],
                          "achieved": achieved_dom, "peak": peak, "unit": "GB/s",
                          "frac": achieved_dom / peak, "traffic": traffic,
                          "peak_source": peak_kind,
@@ -502,7 +516,7 @@ def main():
             "gate_roofline": {"achieved": achieved_gate, "peak": peak, "unit": "GB/s",
                               "frac": achieved_gate / peak, "alg_bytes_per_gate": b_alg_gate,
                               "gate_ms": gate_ms},
-            "kernel_time_share": {KERNEL_NAMES[k]: prof[k][1] / max(1e-9, sum(
+            "kernel_time_share": {KERNEL_NAMES[args.merge_path][k]: prof[k][1] / max(1e-9, sum(
                 prof[j][1] for j in prof)) for k in prof},
             "clocks": clk,
             "e2e": e2e,
@@ -510,6 +524,7 @@ def main():
             "gpu_launches": int(launches),
             "timed_gates": int(gates),
             "table_probes_per_term": (st1["table_probes"] - st0["table_probes"]) / max(terms_in, 1),
+            "repartitions_per_gate": (st1["repartitions"] - st0["repartitions"]) / max(gates, 1),
             "terms_in_timed": int(terms_in),
         }
         print(json.dumps(line), flush=True)

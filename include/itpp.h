@@ -105,6 +105,8 @@ typedef struct {
     uint64_t count;           /* current term count                             */
     uint64_t table_probes;    /* merge-table slots visited (build + lookups)    */
     uint64_t kernel_launches; /* kernels this handle has launched (host count)  */
+    uint64_t repartitions;    /* partitioned merge: scatters run (window starts,
+                               * state changes, partitions past the split limit) */
 } itpp_stats;
 
 /* ---------------------------------------------------------------------------
@@ -218,9 +220,10 @@ itpp_status itpp_get_stats(itpp_handle h, itpp_stats* out);
 /* Kernel timing with CUDA events recorded on the handle's stream around the
  * launches of the gate kernels.  itpp_profile_enable(h, 1) starts (and
  * clears) the accumulation; itpp_profile_read synchronises and returns, for
- * kernel class kid (0 = merge-table build, 1 = branch-emit-merge-truncate,
- * 2 = cap select, 3 = expectation), the number of launches and their total
- * device time in milliseconds. */
+ * kernel class kid, the number of launches and their total device time in
+ * milliseconds.  kid 0: the state scatter (merge_path 0) or the global
+ * merge-table build (merge_path 2); 1: branch-emit-merge-truncate (the whole
+ * sorted merge for merge_path 1); 2: the top-M select; 3: expectation. */
 itpp_status itpp_profile_enable(itpp_handle h, int enable);
 itpp_status itpp_profile_read(itpp_handle h, int kid, uint64_t* launches, double* total_ms);
 

@@ -369,6 +369,7 @@ itpp_status adjoint_w(itpp_ctx* h, int L, int K, const uint64_t* obs_x, const ui
     // ---- forward from the identity, logging counts, snapshot per segment
     DevBuf log;
     if (!log.alloc((size_t)(S + 1) * 8)) return ITPP_ERR_ALLOC;
+    itpp_detail_touch(h);
     if (!chk(launch_reset_identity(s, st))) return ITPP_ERR_CUDA;
     std::vector<DevBuf> snap((size_t)n_seg);
     std::vector<uint64_t> snap_n((size_t)n_seg);
@@ -380,7 +381,7 @@ itpp_status adjoint_w(itpp_ctx* h, int L, int K, const uint64_t* obs_x, const ui
         if (!snap[(size_t)j].alloc((size_t)c * (kb + 8))) return ITPP_ERR_ALLOC;
         PKey<W>* sk = snap[(size_t)j].as<PKey<W>>();
         double* sc = reinterpret_cast<double*>(sk + c);
-        if (!chk(launch_materialize(s, st))) return ITPP_ERR_CUDA;
+        if (!chk((itpp_detail_touch(h), launch_materialize(s, st)))) return ITPP_ERR_CUDA;
         k_adj_snapshot<W><<<grid, 256, 0, st>>>(
             static_cast<const PKey<W>*>(s.keys[0]), s.coef[0],
             static_cast<const PKey<W>*>(s.keys[1]), s.coef[1], s.ctl, sk, sc);
@@ -418,7 +419,7 @@ itpp_status adjoint_w(itpp_ctx* h, int L, int K, const uint64_t* obs_x, const ui
         !chk(cudaMemcpyAsync(d_oz, obs_z, (size_t)m * W * 8, cudaMemcpyHostToDevice, st)) ||
         !chk(cudaMemcpyAsync(d_w, seed, (size_t)m * 8, cudaMemcpyHostToDevice, st)))
         return ITPP_ERR_CUDA;
-    if (!chk(launch_materialize(s, st)) ||
+    if (!chk((itpp_detail_touch(h), launch_materialize(s, st))) ||
         !chk(launch_expect(s, d_ox, d_oz, d_w, m, (int)tsize, d_tab, d_first, d_vals, d_out, st)))
         return ITPP_ERR_CUDA;
     k_adj_wsum<<<1, 32, 0, st>>>(d_first, d_w, m, d_wsum);

@@ -300,6 +300,7 @@ itpp_status itpp_batch_get_stats(itpp_batch_handle h, int b, itpp_stats* o) {
     o->cap_events = c->stat_cap;
     o->count = c->count[c->cur];
     o->table_probes = c->stat_probes;
+    o->repartitions = 0;
     o->kernel_launches = h->launches;
     return (itpp_status)c->status;
 }

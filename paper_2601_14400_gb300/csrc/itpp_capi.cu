@@ -55,6 +55,8 @@ void free_all(itpp_ctx* h) {
     if (h->s.part_keys) cudaFree(h->s.part_keys);
     if (h->s.part_coef) cudaFree(h->s.part_coef);
     if (h->s.part_cursor) cudaFree(h->s.part_cursor);
+    for (int i = 0; i < 2; ++i)
+        if (h->s.part_desc[i]) cudaFree(h->s.part_desc[i]);
     if (h->s.ctl) cudaFree(h->s.ctl);
     if (h->obs_mem) cudaFree(h->obs_mem);
     if (h->sort_mem) cudaFree(h->sort_mem);
@@ -111,9 +113,16 @@ itpp_status launch_one_gate(itpp_ctx* h, int k) {
     const HostGate& g = h->gates[(size_t)k];
     cudaError_t e = cudaSuccess;
     if (h->p.merge_path == 0) {
+        // a window's first gate (or any gate after the state changed
+        // elsewhere) re-partitions; later gates of the window read the
+        // previous gate's segments unless a partition outgrew the limit
+        const int force = g.win_start || h->part_epoch != h->state_epoch ||
+                          h->part_last != k - 1;
         EventPair* ev0 = prof_begin(h, 0);
-        e = launch_part_scatter(h->s, g, h->stream);
+        e = launch_part_scatter(h->s, g, force, h->stream);
         prof_end(h, ev0);
+        h->part_epoch = h->state_epoch;
+        h->part_last = k;
         if (e == cudaSuccess) {
             EventPair* ev1 = prof_begin(h, 1);
             e = launch_part_merge(h->s, g, h->stream);
@@ -299,12 +308,18 @@ itpp_status itpp_create(int n, const uint64_t* gate_x, const uint64_t* gate_z,
     ok &= ok && cudaMalloc(reinterpret_cast<void**>(&s.ctl), sizeof(DevCtl)) == cudaSuccess;
     ok &= ok && cudaMallocHost(reinterpret_cast<void**>(&h->h_ctl), sizeof(DevCtl)) == cudaSuccess;
     if (ok && p->merge_path == 0) {
-        s.part_cap = p->cap_M + p->cap_M / 2 + 65536;
+        // the scatter buffer: partitions of a fixed stride, 2.5x the mean
+        // partition at the bound (a window group adds up to 4^sites terms)
+        s.part_cap = 2 * p->cap_M + p->cap_M / 2 + (1ULL << 18);
         s.part_max = partition_max(W, p->cap_M);
         ok &= cudaMalloc(&s.part_keys, s.part_cap * 16 * W) == cudaSuccess;
         ok &= ok && cudaMalloc(reinterpret_cast<void**>(&s.part_coef), s.part_cap * 8) == cudaSuccess;
         ok &= ok && cudaMalloc(reinterpret_cast<void**>(&s.part_cursor),
                                (size_t)s.part_max * sizeof(unsigned int)) == cudaSuccess;
+        for (int i = 0; i < 2; ++i)
+            ok &= ok && cudaMalloc(reinterpret_cast<void**>(&s.part_desc[i]),
+                                   (size_t)s.part_max * sizeof(PartDesc)) == cudaSuccess;
+        plan_windows(W, h->gates);
     }
     if (ok && p->merge_path == 1) {
         h->sort_bytes = sorted_scratch_bytes(W, s.buf_cap);
@@ -361,13 +376,14 @@ itpp_status itpp_reset(itpp_handle h) {
     if (!h) return ITPP_ERR_ARG;
     if (h->sticky == ITPP_ERR_CUDA) return h->sticky;
     h->sticky = ITPP_OK;
+    itpp_detail_touch(h);
     return launch_reset_identity(h->s, h->stream) == cudaSuccess ? ITPP_OK : cuda_fail(h);
 }
 
 itpp_status itpp_truncate(itpp_handle h, double delta) {
     if (!h || !(delta >= 0.0) || !std::isfinite(delta)) return ITPP_ERR_ARG;
     if (h->sticky) return h->sticky;
-    if (launch_materialize(h->s, h->stream) != cudaSuccess) return cuda_fail(h);
+    if ((itpp_detail_touch(h), launch_materialize(h->s, h->stream)) != cudaSuccess) return cuda_fail(h);
     return launch_truncate(h->s, delta + 0.0, h->stream) == cudaSuccess ? ITPP_OK : cuda_fail(h);
 }
 
@@ -394,6 +410,7 @@ itpp_status itpp_get_stats(itpp_handle h, itpp_stats* o) {
     o->cap_events = c.stat_cap;
     o->count = c.count[c.cur];
     o->table_probes = c.stat_probes;
+    o->repartitions = c.stat_scatters;
     o->kernel_launches = h->launches;
     return st;
 }
@@ -401,7 +418,7 @@ itpp_status itpp_get_stats(itpp_handle h, itpp_stats* o) {
 itpp_status itpp_get_terms(itpp_handle h, uint64_t* x, uint64_t* z, double* c,
                            uint64_t capacity, uint64_t* count) {
     if (!h || !count) return ITPP_ERR_ARG;
-    if (!h->sticky && launch_materialize(h->s, h->stream) != cudaSuccess) return cuda_fail(h);
+    if (!h->sticky && (itpp_detail_touch(h), launch_materialize(h->s, h->stream)) != cudaSuccess) return cuda_fail(h);
     itpp_status st = sync_ctl(h);
     if (st) return st;
     const uint64_t n = h->h_ctl->count[h->h_ctl->cur];
@@ -436,6 +453,7 @@ itpp_status itpp_set_terms(itpp_handle h, const uint64_t* x, const uint64_t* z, 
         cudaMemcpyAsync(dz, z, kb, cudaMemcpyHostToDevice, h->stream) != cudaSuccess ||
         cudaMemcpyAsync(dc, c, (size_t)count * 8, cudaMemcpyHostToDevice, h->stream) != cudaSuccess)
         return cuda_fail(h);
+    itpp_detail_touch(h);
     if (launch_import(h->s, dx, dz, dc, count, h->stream) != cudaSuccess) return cuda_fail(h);
     h->sticky = ITPP_OK;
     itpp_status st = sync_ctl(h);
@@ -456,7 +474,7 @@ itpp_status itpp_expect_device(itpp_handle h, const uint64_t* d_ox, const uint64
     itpp_status st = ensure_obs(h, m, h->s.W);
     if (st) return st;
     ObsPtrs o = obs_layout(h, m, h->s.W);
-    if (launch_materialize(h->s, h->stream) != cudaSuccess) return cuda_fail(h);
+    if ((itpp_detail_touch(h), launch_materialize(h->s, h->stream)) != cudaSuccess) return cuda_fail(h);
     EventPair* ev = prof_begin(h, 3);
     cudaError_t e = launch_expect(h->s, d_ox, d_oz, d_ow, m, o.tsize, o.tab, o.first, o.vals,
                                   d_out, h->stream);
@@ -479,7 +497,7 @@ static itpp_status expect_host(itpp_handle h, const uint64_t* ox, const uint64_t
     if (ow && cudaMemcpyAsync(o.ow, ow, (size_t)m * 8, cudaMemcpyHostToDevice, h->stream) !=
                   cudaSuccess)
         return cuda_fail(h);
-    if (launch_materialize(h->s, h->stream) != cudaSuccess) return cuda_fail(h);
+    if ((itpp_detail_touch(h), launch_materialize(h->s, h->stream)) != cudaSuccess) return cuda_fail(h);
     EventPair* ev = prof_begin(h, 3);
     cudaError_t e = launch_expect(h->s, o.ox, o.oz, ow ? o.ow : nullptr, m, o.tsize, o.tab,
                                   o.first, o.vals, o.out, h->stream);

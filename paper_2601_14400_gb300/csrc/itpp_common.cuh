@@ -73,6 +73,7 @@ struct DevCtl {
     // statistics
     unsigned long long stat_gates, stat_in, stat_out, stat_peak, stat_cap;
     unsigned long long stat_probes;
+    unsigned long long stat_scatters;
     // top-M select state
     int sel_active;
     int sel_pass;
@@ -95,6 +96,11 @@ struct DevCtl {
     unsigned long long pend_T;
     uint64_t pend_tie_key[4];
     uint64_t sel_tie_key[4];         // largest kept tie key (x..., z...)
+    // partitioned merge: where the next merge finds its partitions
+    unsigned int part_P;             // partitions of the current state
+    int part_from_scatter;           // 1: in the scatter buffer; 0: segments of the state
+    int part_over;                   // this gate left a partition above the split limit
+    int need_scatter;                // ... so the next gate re-partitions
     unsigned long long sel_hist[kSelBins];
     unsigned long long tie_hist[kTieBins];
 };

@@ -43,6 +43,11 @@ struct itpp_ctx {
     void* sort_mem = nullptr;
     uint64_t sort_bytes = 0;
     uint64_t launches = 0;   // kernels launched by this handle
+    // partitioned merge: the state's partitions are valid for the window of
+    // gate part_last while part_epoch == state_epoch; anything else that
+    // changes the state bumps state_epoch
+    uint64_t state_epoch = 1, part_epoch = 0;
+    int part_last = -1;
     // profiling
     bool prof = false;
     std::vector<EventPair> ev[kKinds];
@@ -55,3 +60,5 @@ struct itpp_ctx {
 // Helpers of the C ABI used by more than one translation unit.
 itpp_status itpp_detail_sync_ctl(itpp_ctx* h);
 itpp_status itpp_detail_launch_gate(itpp_ctx* h, int k);
+// The state changed outside a window's merges (partitions must be rebuilt).
+inline void itpp_detail_touch(itpp_ctx* h) { ++h->state_epoch; }

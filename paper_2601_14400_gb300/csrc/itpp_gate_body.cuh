@@ -247,7 +247,9 @@ __device__ __forceinline__ void gate_tile(uint64_t t, uint64_t n,
 // table generation, statistics and the term bound.  Returns 1 when the top-M
 // select must run.
 __device__ __forceinline__ int post_one(DevCtl* ctl, uint64_t cap_M, int cap_policy) {
-    ctl->pend = 0;   // a deferred select was applied by this gate's scatter
+    ctl->pend = 0;   // a deferred select was applied by this gate's scatter or merge
+    ctl->need_scatter = ctl->part_over;
+    ctl->part_over = 0;
     const int cur = ctl->cur, nxt = cur ^ 1;
     const unsigned long long n_in = ctl->count[cur], n_out = ctl->count[nxt];
     ctl->cur = nxt;

@@ -2,11 +2,20 @@
 #pragma once
 
 #include <cstdint>
+#include <vector>
 #include <cuda_runtime.h>
 
 namespace itpp {
 
 struct DevCtl;
+
+// One partition of the state as a gate of a window wrote it (a contiguous
+// segment of the state buffer).
+struct PartDesc {
+    unsigned long long off;   // first term in the state buffer
+    unsigned int cnt;         // terms stored
+    unsigned int pad;
+};
 
 // Device resources of one propagation (or of one batch instance table).
 struct DeviceState {
@@ -26,6 +35,7 @@ struct DeviceState {
     void* part_keys = nullptr;        // PKey<W>[part_cap]
     double* part_coef = nullptr;      // double[part_cap]
     unsigned int* part_cursor = nullptr;   // [part_max]
+    PartDesc* part_desc[2] = {nullptr, nullptr};   // [part_max] per state buffer
     uint64_t part_cap = 0;
     uint32_t part_max = 0;
     // top-M select leaves its kept set as a predicate for the next scatter
@@ -38,6 +48,11 @@ struct HostGate {
     double ch = 1, msh = 0;  // cosh(theta), -sinh(theta)
     double sh = 0, chd = 1;  // d ch / d theta = sinh(theta), -d msh / d theta = cosh(theta)
     int qyy = 0;
+    // the window of consecutive gates this gate belongs to (partitioned merge)
+    uint64_t keep_x[2] = {~0ULL, ~0ULL}, keep_z[2] = {~0ULL, ~0ULL};   // key bits hashed
+    int pair_mode = 1;       // 1: the gate alone, partitioned by its pair key
+    int win_sites = 0;       // sites of the window (mask mode)
+    int win_start = 1;       // first gate of its window
 };
 
 // One elementary gate: merge-table build, branch-emit-merge-truncate, post.
@@ -46,9 +61,16 @@ cudaError_t launch_gate_main(const DeviceState& s, const HostGate& g, cudaStream
 cudaError_t launch_gate_post(const DeviceState& s, cudaStream_t st);
 // Partitioned merge: scatter by pair key, then one shared-memory table per
 // partition (the default merge of a single propagation).
-cudaError_t launch_part_scatter(const DeviceState& s, const HostGate& g, cudaStream_t st);
+// force = 1 re-partitions unconditionally (first gate of a window, or the
+// state changed outside the window); force = 0 only when the previous gate
+// left a partition above the split limit.
+cudaError_t launch_part_scatter(const DeviceState& s, const HostGate& g, int force,
+                                cudaStream_t st);
 cudaError_t launch_part_merge(const DeviceState& s, const HostGate& g, cudaStream_t st);
 uint32_t partition_max(int W, uint64_t cap_M);
+// Group consecutive gates into windows of at most a few sites (sets the
+// window fields of every gate).
+void plan_windows(int W, std::vector<HostGate>& gates);
 // Top-M select and compaction (no-ops on the device when the bound holds).
 cudaError_t launch_cap(const DeviceState& s, cudaStream_t st);
 int cap_launches(const DeviceState& s);

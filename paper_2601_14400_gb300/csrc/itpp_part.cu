@@ -1,18 +1,23 @@
 // itpp_part.cu -- the per-gate merge with the table in shared memory.
 //
-// A gate's merge only ever pairs a string K with its partner Q.K, and both
-// have the same "pair key": the member of {K, Q.K} whose pivot bit (the
-// lowest set bit of Q's masks) is clear.  So the state is first scattered
-// into hash partitions of the pair key (one streaming pass, one atomic per
-// term on the partition's cursor), and then a persistent kernel takes one
-// partition at a time per CTA: it builds the partition's merge table in
-// shared memory, then runs the branch-emit-merge-truncate tile body
-// (itpp_gate_body.cuh) with lookups served from shared memory.  No table
-// access reaches HBM; the partition's terms are read twice, the second time
-// from L2.  Partitions have a fixed stride in the scatter buffer, sized 1.5x
-// the mean partition, so hash-balanced states never overflow one; if one
-// does (or a partition's commuting terms exceed the shared table), the
-// device status reports ITPP_ERR_CAPACITY.
+// A gate's merge only pairs a string K with its partner QK (Sec. II.B: a
+// commuting string keeps cosh(theta) of itself and sends -sinh(theta) s to QK).
+// Take a window of consecutive gates whose strings act on at most a few
+// sites S, and group the state by the key with the sites of S cleared: K, QK
+// and every child under any gate of the window share that group.  The state
+// is scattered once per window into hash partitions of that masked key (one
+// streaming pass, one atomic per term on the partition's cursor), and then
+// every gate of the window runs a persistent kernel that takes one partition
+// at a time per CTA: the partition's terms stay in registers, the commuting
+// ones publish (key, child for the partner) in a shared-memory table, every
+// term merges with its partner's child, and the kept children of the
+// partition are written as one contiguous segment of the next state buffer
+// (one atomic per partition).  The segments are the partitions of the next
+// gate of the window, so no scatter runs between the gates of a window.  A
+// group holds at most 4^|S| terms; a partition whose output outgrows the
+// shared table's limit makes the next gate re-partition.  A gate acting on
+// more sites than a window allows is a window of its own, partitioned by its
+// pair key (the member of {K, QK} with the gate's lowest bit clear).
 #include "itpp_common.cuh"
 #include "itpp_gate_body.cuh"
 #include "itpp_launch.h"
@@ -22,12 +27,17 @@ namespace itpp {
 namespace {
 
 
-// Shared-table geometry per word count: slots, and the mean partition size
-// the scatter aims for (commuting terms of a partition stay well under 70%
-// of the slots even when every term commutes).
+// Shared-table geometry per word count: slots, the mean partition size the
+// scatter aims for, the largest partition output a following gate of the
+// window may read (its commuting terms stay under 70% of the slots), and the
+// largest window (sites; a group holds at most 4^sites terms).
 template <int W> struct PartGeom;
-template <> struct PartGeom<1> { static constexpr int kSlots = 2048; static constexpr int kTarget = 700; };
-template <> struct PartGeom<2> { static constexpr int kSlots = 1024; static constexpr int kTarget = 350; };
+template <> struct PartGeom<1> {
+    static constexpr int kSlots = 2048, kTarget = 600, kSplit = 1400, kWinSites = 5;
+};
+template <> struct PartGeom<2> {
+    static constexpr int kSlots = 1024, kTarget = 300, kSplit = 700, kWinSites = 4;
+};
 
 template <int W>
 constexpr size_t part_smem_bytes() {
@@ -50,67 +60,135 @@ __device__ __forceinline__ PartPlan part_plan(uint64_t n, uint64_t pbuf_cap, uin
     return pl;
 }
 
+// The partition function of a window: the hash of the key with the
+// window's sites cleared, or (pair mode) of the gate's pair key.
 template <int W>
-struct PivotArg {
-    int word;        // 0..W-1: x[word]; W..2W-1: z[word-W]; -1: Q is the identity
+struct PartFn {
+    uint64_t kx[W], kz[W];   // bits kept by the mask
+    int pair;                // 1: pair-key mode
+    int sites;               // sites of the window (mask mode)
+    int word;                // pivot: 0..W-1 x[word], W..2W-1 z[word-W]; -1: Q = I
     uint64_t bit;
 };
 
+// Mask mode needs many more possible groups than terms: a group (the terms
+// with one pattern outside the window) holds up to 4^sites of them, and a
+// partition that collects several large groups could outgrow its stride or
+// the shared table.  So the window's mask is used only while
+// 4^(n - sites) >= 64 N; a denser state (a small or saturated chain) falls
+// back to the pair key of the window's first gate, valid for that gate only.
+__device__ __forceinline__ bool window_fits(int n_sites, int w_sites, uint64_t n_terms) {
+    const int free_bits = 2 * (n_sites - w_sites);
+    const int need_bits = 6 + (n_terms > 1 ? 64 - __clzll((long long)(n_terms - 1)) : 0);
+    return free_bits >= need_bits;
+}
+
 template <int W>
 __device__ __forceinline__ uint32_t part_of(const PKey<W>& K, const GateArg<W>& g,
-                                            const PivotArg<W>& pv, uint32_t P) {
-    PKey<W> k = K;
-    if (pv.word >= 0) {
-        const uint64_t w = pv.word < W ? K.x[pv.word] : K.z[pv.word - W];
-        if (w & pv.bit) k = key_xor(K, g);
+                                            const PartFn<W>& f, uint32_t P) {
+    PKey<W> k;
+    if (f.pair) {
+        k = K;
+        if (f.word >= 0) {
+            const uint64_t w = f.word < W ? K.x[f.word] : K.z[f.word - W];
+            if (w & f.bit) k = key_xor(K, g);
+        }
+    } else {
+#pragma unroll
+        for (int w = 0; w < W; ++w) { k.x[w] = K.x[w] & f.kx[w]; k.z[w] = K.z[w] & f.kz[w]; }
     }
     const uint64_t h = key_hash(k);   // 32 significant bits
     return (uint32_t)((h * (uint64_t)P) >> 32);
 }
 
+// The kept set of a deferred top-M select, applied where terms are read.
+template <int W>
+struct Pending {
+    bool on, all_ties;
+    unsigned long long T;
+    PKey<W> tk;
+};
+
+template <int W>
+__device__ __forceinline__ Pending<W> pending_of(const DevCtl* ctl) {
+    Pending<W> q;
+    q.on = ctl->pend != 0;
+    q.all_ties = ctl->pend_all_ties != 0;
+    q.T = ctl->pend_T;
+#pragma unroll
+    for (int w = 0; w < W; ++w) { q.tk.x[w] = ctl->pend_tie_key[w]; q.tk.z[w] = ctl->pend_tie_key[W + w]; }
+    return q;
+}
+
 }  // namespace
 
-// Scatter the current state into partitions of the gate's pair key.
+// Scatter the current state into the partitions of a window (force), or,
+// inside a window, only when the previous gate left a partition above the
+// split limit; otherwise the next merge reads the previous merge's segments.
 template <int W>
 __global__ void __launch_bounds__(256)
 k_part_scatter(Bufs<W> B, DevCtl* ctl, PKey<W>* pk, double* pc, unsigned int* cursor,
-               uint64_t pbuf_cap, uint32_t p_max, GateArg<W> g, PivotArg<W> pv) {
+               uint64_t pbuf_cap, uint32_t p_max, GateArg<W> g, PartFn<W> f, int force,
+               int n_sites) {
     if (ctl->status) return;
     const int cur = ctl->cur;
+    if (!force && !ctl->need_scatter) {
+        if (blockIdx.x == 0 && threadIdx.x == 0) {
+            ctl->count[cur ^ 1] = 0ULL;
+            ctl->part_from_scatter = 0;
+        }
+        return;
+    }
     const uint64_t n = live_count(ctl, cur);
     const PartPlan pl = part_plan(n, pbuf_cap, p_max, PartGeom<W>::kTarget);
-    if (blockIdx.x == 0 && threadIdx.x == 0) ctl->count[cur ^ 1] = 0ULL;
+    const bool fallback = !f.pair && !window_fits(n_sites, f.sites, n);
+    if (fallback) f.pair = 1;
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        ctl->count[cur ^ 1] = 0ULL;
+        ctl->part_from_scatter = 1;
+        ctl->part_P = pl.P;
+        ctl->stat_scatters += 1;
+        if (fallback) ctl->part_over = 1;   // the partitions hold for this gate only
+    }
     const PKey<W>* __restrict__ kin = B.k[cur];
     const double* __restrict__ cin = B.c[cur];
     // a deferred top-M select: scan every stored term, keep its kept set
-    const bool pend = ctl->pend;
+    const Pending<W> pd = pending_of<W>(ctl);
     uint64_t n_scan = n;
-    unsigned long long T = 0;
-    bool all_ties = false;
-    PKey<W> tk;
-    if (pend) {
-        n_scan = ctl->pend_n < ctl->buf_cap ? ctl->pend_n : ctl->buf_cap;
-        T = ctl->pend_T;
-        all_ties = ctl->pend_all_ties;
-#pragma unroll
-        for (int w = 0; w < W; ++w) { tk.x[w] = ctl->pend_tie_key[w]; tk.z[w] = ctl->pend_tie_key[W + w]; }
-    }
-    for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n_scan;
-         i += (uint64_t)gridDim.x * blockDim.x) {
-        const PKey<W> K = load_key_stream(kin + i);
-        const double c = __ldcs(cin + i);
-        if (pend && !cap_keep(K, c, T, all_ties, tk)) {
-            if (key_is_zero(K)) set_status(ctl, ST_TRACE_ZERO, 42);
-            continue;
+    if (pd.on) n_scan = ctl->pend_n < ctl->buf_cap ? ctl->pend_n : ctl->buf_cap;
+    // whole warps iterate together (the cursor claim below is warp-wide)
+    const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+    const unsigned int lt = (1u << (threadIdx.x & 31)) - 1u;
+    for (uint64_t i0 = (uint64_t)blockIdx.x * blockDim.x; i0 < n_scan; i0 += stride) {
+        const uint64_t i = i0 + threadIdx.x;
+        PKey<W> K;
+        double c = 0.0;
+        bool live = i < n_scan;
+        if (live) {
+            K = load_key_stream(kin + i);
+            c = __ldcs(cin + i);
+            if (pd.on && !cap_keep(K, c, pd.T, pd.all_ties, pd.tk)) {
+                if (key_is_zero(K)) set_status(ctl, ST_TRACE_ZERO, 42);
+                live = false;
+            }
         }
-        const uint32_t p = part_of(K, g, pv, pl.P);
-        const unsigned int pos = atomicAdd(cursor + p, 1u);
-        if (pos < pl.R) {
-            const uint64_t d = (uint64_t)p * pl.R + pos;
-            pk[d] = K;
-            pc[d] = c;
-        } else {
-            set_status(ctl, ST_CAPACITY, 40);
+        // one cursor claim per distinct partition in the warp: terms of one
+        // group arrive together and would otherwise serialise on its cursor
+        const uint32_t p = live ? part_of(K, g, f, pl.P) : 0xffffffffu;
+        const unsigned int peers = __match_any_sync(0xffffffffu, p);
+        const int leader = __ffs(peers) - 1;
+        unsigned int base = 0;
+        if (live && (threadIdx.x & 31) == leader) base = atomicAdd(cursor + p, __popc(peers));
+        base = __shfl_sync(0xffffffffu, base, leader);
+        if (live) {
+            const unsigned int pos = base + __popc(peers & lt);
+            if (pos < pl.R) {
+                const uint64_t d = (uint64_t)p * pl.R + pos;
+                pk[d] = K;
+                pc[d] = c;
+            } else {
+                set_status(ctl, ST_CAPACITY, 40);
+            }
         }
     }
 }
@@ -131,18 +209,22 @@ struct PartItem {
 
 template <int W>
 __device__ __forceinline__ PartItem<W> part_item(const PKey<W>* kp, const double* cp, uint64_t i,
-                                                 uint64_t np, const GateArg<W>& g, double rnorm) {
+                                                 uint64_t np, const GateArg<W>& g, double rnorm,
+                                                 const Pending<W>& pd, DevCtl* ctl) {
     PartItem<W> it;
     double raw = 0.0;
     bool neg = false;
 #pragma unroll
     for (int w = 0; w < W; ++w) { it.K.x[w] = 0; it.K.z[w] = 0; }
-    it.live = i < np;
+    it.live = false;
     it.comm = false;
-    if (it.live) {
+    if (i < np) {
         it.K = load_key_stream(kp + i);
         raw = __ldcs(cp + i);
-        it.comm = commutes(it.K, g);
+        // a deferred top-M select drops the terms outside its kept set here
+        it.live = !pd.on || cap_keep(it.K, raw, pd.T, pd.all_ties, pd.tk);
+        if (!it.live && key_is_zero(it.K)) set_status(ctl, ST_TRACE_ZERO, 43);
+        it.comm = it.live && commutes(it.K, g);
         neg = it.comm && product_negative(it.K, g);
     }
     // the same double-precision operations on every lane; the identity's
@@ -154,12 +236,33 @@ __device__ __forceinline__ PartItem<W> part_item(const PKey<W>* kp, const double
     return it;
 }
 
+// Slot of a key in a partition's table (at most a few thousand slots): a
+// multiply-xor of the key's 32-bit halves and one xorshift-multiply round,
+// about a third of the instructions of the full key hash.  Partitions are
+// chosen by the full hash of a different key (masked or pair key), so the
+// two are independent.
+template <int W>
+__device__ __forceinline__ uint32_t slot_hash(const PKey<W>& k) {
+    constexpr uint32_t C[8] = {0x9E3779B1u, 0x85EBCA77u, 0xC2B2AE3Du, 0x27D4EB2Fu,
+                               0x165667B1u, 0xD3A2646Du, 0xFD7046C5u, 0xB55A4F09u};
+    uint32_t h = 0;
+#pragma unroll
+    for (int w = 0; w < W; ++w) {
+        h ^= (uint32_t)k.x[w] * C[4 * w] ^ (uint32_t)(k.x[w] >> 32) * C[4 * w + 1];
+        h ^= (uint32_t)k.z[w] * C[4 * w + 2] ^ (uint32_t)(k.z[w] >> 32) * C[4 * w + 3];
+    }
+    h ^= h >> 15;
+    h *= 0x2C1B3C6Du;
+    h ^= h >> 12;
+    return h;
+}
+
 // Shared-memory table of one partition: commuting keys and their b.
 template <int W>
 __device__ __forceinline__ bool part_insert(const PartItem<W>& it, PKey<W>* t_keys, double* t_b,
                                             uint32_t* t_tag) {
     constexpr uint32_t S = PartGeom<W>::kSlots;
-    uint32_t h = (uint32_t)key_hash(it.K) & (S - 1);
+    uint32_t h = slot_hash(it.K) & (S - 1);
     for (uint32_t q = 0; q < S; ++q) {
         if (atomicCAS(t_tag + h, 0u, 1u) == 0u) {
             t_keys[h] = it.K;
@@ -175,7 +278,7 @@ template <int W>
 __device__ __forceinline__ bool part_find(const PKey<W>& P, const PKey<W>* t_keys,
                                           const double* t_b, const uint32_t* t_tag, double* out) {
     constexpr uint32_t S = PartGeom<W>::kSlots;
-    uint32_t h = (uint32_t)key_hash(P) & (S - 1);
+    uint32_t h = slot_hash(P) & (S - 1);
     for (uint32_t q = 0; q < S; ++q) {
         if (t_tag[h] == 0u) return false;
         if (key_eq(t_keys[h], P)) { *out = t_b[h]; return true; }
@@ -199,91 +302,178 @@ __device__ __forceinline__ void part_children(const PartItem<W>& it, const GateA
     *emit_b = it.comm && !found;
 }
 
-// One partition at a time per CTA: the partition's items stay in registers
-// (BLOCK x IPT of them; a longer partition reloads the rest), the commuting
-// ones publish (key, b) in a shared-memory table, then every item merges
-// with its partner's b and the kept children are written out.
+// Flags of one item after the merge: bit 0 keeps the self child (merged
+// value va), bit 1 emits the QK child (value b).  The identity is always
+// kept and its merged value is the next normaliser.
+template <int W>
+__device__ __forceinline__ uint32_t part_flags(const PartItem<W>& it, const GateArg<W>& g,
+                                               const PKey<W>* t_keys, const double* t_b,
+                                               const uint32_t* t_tag, unsigned long long dbits,
+                                               DevCtl* ctl, int nxt, double* va) {
+    bool eb;
+    part_children(it, g, t_keys, t_b, t_tag, va, &eb);
+    if (!it.live) return 0u;
+    bool keep_a = above(*va, dbits);
+    const bool keep_b = eb && above(it.b, dbits);
+    if (key_is_zero(it.K)) {
+        ctl->norm[nxt] = *va;
+        if (!keep_a) set_status(ctl, ST_TRACE_ZERO, 1);
+        keep_a = true;
+    }
+    return (keep_a ? 1u : 0u) | (keep_b ? 2u : 0u);
+}
+
+template <int W>
+__device__ __forceinline__ void part_write(const PartItem<W>& it, const GateArg<W>& g, double va,
+                                           uint32_t fl, PKey<W>* kout, double* cout,
+                                           uint64_t pos) {
+    if (fl & 1u) {
+        store_key_stream(kout + pos, it.K);
+        __stcs(cout + pos, va);
+        ++pos;
+    }
+    if (fl & 2u) {
+        store_key_stream(kout + pos, key_xor(it.K, g));
+        __stcs(cout + pos, it.b);
+    }
+}
+
+// Exclusive block scan with one barrier: every warp writes its total, and
+// after the barrier every thread sums the totals of the warps before its own
+// (s_warp may be rewritten only after the caller's next barrier).
+template <int BLOCK>
+__device__ __forceinline__ uint32_t scan_one_barrier(uint32_t v, uint32_t* s_warp,
+                                                     uint32_t* total) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    uint32_t x = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= o) x += y;
+    }
+    if (lane == 31) s_warp[warp] = x;
+    __syncthreads();
+    uint32_t before = 0, tot = 0;
+#pragma unroll
+    for (int w = 0; w < BLOCK / 32; ++w) {
+        const uint32_t t = s_warp[w];
+        before += w < warp ? t : 0u;
+        tot += t;
+    }
+    *total = tot;
+    return before + x - v;
+}
+
+// One partition at a time per CTA.  The partition comes from the scatter
+// buffer (fixed stride, cursor) or is a segment the previous gate of the
+// window wrote (descriptor).  Its items stay in registers (BLOCK x IPT of
+// them; a longer partition takes a two-pass path that reloads), the
+// commuting ones publish (key, b) in a shared-memory table, then every item
+// merges with its partner's b, and the kept children of the partition go to
+// one contiguous segment of the next state buffer, recorded as the
+// partition's descriptor for the next gate.  Four barriers per partition:
+// table built; warp totals written; segment claimed; segment written and
+// table cleared for the next partition.
 template <int W, int kPBlock, int kPIpt>
-__global__ void __launch_bounds__(kPBlock)
+__global__ void __launch_bounds__(kPBlock, (W == 1 ? 1536 : 1024) / kPBlock)
 k_gate_part(const PKey<W>* __restrict__ pk, const double* __restrict__ pc,
-            const unsigned int* __restrict__ cursor, Bufs<W> B, DevCtl* ctl,
-            uint64_t pbuf_cap, uint32_t p_max, GateArg<W> g, double delta, uint64_t cap_out) {
+            unsigned int* __restrict__ cursor, uint64_t pbuf_cap, PartDesc* desc0,
+            PartDesc* desc1, Bufs<W> B, DevCtl* ctl, GateArg<W> g, double delta,
+            uint64_t cap_out) {
     extern __shared__ __align__(16) unsigned char smem[];
     constexpr int S = PartGeom<W>::kSlots;
     constexpr uint64_t CHUNK = (uint64_t)kPBlock * kPIpt;
+    // a segment above this size makes the next gate re-partition: the
+    // shared table's limit, or twice the register chunk for small CTAs
+    constexpr uint32_t kSplitAt = (uint32_t)(2 * CHUNK) < (uint32_t)PartGeom<W>::kSplit
+                                      ? (uint32_t)(2 * CHUNK) : (uint32_t)PartGeom<W>::kSplit;
     PKey<W>* t_keys = reinterpret_cast<PKey<W>*>(smem);
     double* t_b = reinterpret_cast<double*>(t_keys + S);
     uint32_t* t_tag = reinterpret_cast<uint32_t*>(t_b + S);
+    __shared__ uint32_t s_warp[kPBlock / 32];
     __shared__ uint32_t s_scan[kPBlock / 32];
     __shared__ unsigned long long s_base;
+    __shared__ uint32_t s_total;
     if (ctl->status) return;
-    const int cur = ctl->cur;
-    const uint64_t n = live_count(ctl, cur);
-    const PartPlan pl = part_plan(n, pbuf_cap, p_max, PartGeom<W>::kTarget);
+    const int cur = ctl->cur, nxt = cur ^ 1;
+    const bool from_scatter = ctl->part_from_scatter != 0;
+    const uint32_t P = ctl->part_P;
+    const uint64_t R = P ? pbuf_cap / P : 0;
+    const PartDesc* __restrict__ din = cur ? desc1 : desc0;
+    PartDesc* __restrict__ dout = cur ? desc0 : desc1;
     const double rnorm = ctl->rnorm[cur];
     const unsigned long long dbits = (unsigned long long)__double_as_longlong(delta);
-    PKey<W>* __restrict__ kout = B.k[cur ^ 1];
-    double* __restrict__ cout = B.c[cur ^ 1];
-    for (uint32_t p = blockIdx.x; p < pl.P; p += gridDim.x) {
-        uint64_t np = cursor[p];
-        if (np > pl.R) np = pl.R;
-        const PKey<W>* kp = pk + (uint64_t)p * pl.R;
-        const double* cp = pc + (uint64_t)p * pl.R;
+    const Pending<W> pd = pending_of<W>(ctl);
+    PKey<W>* __restrict__ kout = B.k[nxt];
+    double* __restrict__ cout = B.c[nxt];
+    for (int s2 = threadIdx.x; s2 < S; s2 += kPBlock) t_tag[s2] = 0u;
+    __syncthreads();
+    for (uint32_t p = blockIdx.x; p < P; p += gridDim.x) {
+        const PKey<W>* kp;
+        const double* cp;
+        uint64_t np;
+        if (from_scatter) {
+            np = cursor[p];
+            if (np > R) np = R;
+            kp = pk + (uint64_t)p * R;
+            cp = pc + (uint64_t)p * R;
+        } else {
+            np = din[p].cnt;
+            kp = B.k[cur] + din[p].off;
+            cp = B.c[cur] + din[p].off;
+        }
         // warm L2 with the partition this CTA takes next
         const uint32_t pn = p + gridDim.x;
-        if (pn < pl.P) {
-            uint64_t nn = cursor[pn];
-            if (nn > pl.R) nn = pl.R;
-            const char* nk = reinterpret_cast<const char*>(pk + (uint64_t)pn * pl.R);
-            const char* nc = reinterpret_cast<const char*>(pc + (uint64_t)pn * pl.R);
+        if (pn < P) {
+            uint64_t nn;
+            const char *nk, *nc;
+            if (from_scatter) {
+                nn = cursor[pn];
+                if (nn > R) nn = R;
+                nk = reinterpret_cast<const char*>(pk + (uint64_t)pn * R);
+                nc = reinterpret_cast<const char*>(pc + (uint64_t)pn * R);
+            } else {
+                nn = din[pn].cnt;
+                nk = reinterpret_cast<const char*>(B.k[cur] + din[pn].off);
+                nc = reinterpret_cast<const char*>(B.c[cur] + din[pn].off);
+            }
             for (uint64_t b = (uint64_t)threadIdx.x * 128; b < nn * sizeof(PKey<W>); b += 128 * kPBlock)
                 asm volatile("prefetch.global.L2 [%0];" :: "l"(nk + b));
             for (uint64_t b = (uint64_t)threadIdx.x * 128; b < nn * sizeof(double); b += 128 * kPBlock)
                 asm volatile("prefetch.global.L2 [%0];" :: "l"(nc + b));
         }
-        for (int s2 = threadIdx.x; s2 < S; s2 += kPBlock) t_tag[s2] = 0u;
-        __syncthreads();
-        // items j*BLOCK + tid (coalesced), kept in registers
-        PartItem<W> it[kPIpt];
         bool ok = true;
-#pragma unroll
-        for (int j = 0; j < kPIpt; ++j) {
-            it[j] = part_item(kp, cp, (uint64_t)j * kPBlock + threadIdx.x, np, g, rnorm);
-            if (it[j].comm) ok &= part_insert(it[j], t_keys, t_b, t_tag);
-        }
-        for (uint64_t i = CHUNK + threadIdx.x; i < np; i += kPBlock) {
-            const PartItem<W> x = part_item(kp, cp, i, np, g, rnorm);
-            if (x.comm) ok &= part_insert(x, t_keys, t_b, t_tag);
-        }
-        if (!ok) set_status(ctl, ST_CAPACITY, 41);
-        __syncthreads();
-        // the chunk held in registers, then (rarely) the rest of a long partition
-        for (uint64_t c0 = 0; c0 < np; c0 += CHUNK) {
-            double va[kPIpt];
-            bool eb[kPIpt];
-            uint32_t flags = 0;
+        if (np <= CHUNK) {
+            // the whole partition in registers, items j*BLOCK + tid (coalesced)
+            PartItem<W> it[kPIpt];
 #pragma unroll
             for (int j = 0; j < kPIpt; ++j) {
-                if (c0) it[j] = part_item(kp, cp, c0 + (uint64_t)j * kPBlock + threadIdx.x, np, g, rnorm);
-                part_children(it[j], g, t_keys, t_b, t_tag, &va[j], &eb[j]);
-                bool keep_a = above(va[j], dbits);
-                const bool keep_b = eb[j] && above(it[j].b, dbits);
-                if (it[j].live) {
-                    if (key_is_zero(it[j].K)) {
-                        // the identity: its merged coefficient is the new trace
-                        ctl->norm[cur ^ 1] = va[j];
-                        if (!keep_a) set_status(ctl, ST_TRACE_ZERO, 1);
-                        keep_a = true;
-                    }
-                    flags |= (keep_a ? 1u : 0u) << (2 * j);
-                    flags |= (keep_b ? 1u : 0u) << (2 * j + 1);
-                }
+                it[j] = part_item(kp, cp, (uint64_t)j * kPBlock + threadIdx.x, np, g, rnorm, pd, ctl);
+                if (it[j].comm) ok &= part_insert(it[j], t_keys, t_b, t_tag);
+            }
+            if (!ok) set_status(ctl, ST_CAPACITY, 41);
+            __syncthreads();                                   // (1) table built
+            // every thread has read the cursor: leave it zero for the next scatter
+            if (from_scatter && threadIdx.x == 0) cursor[p] = 0u;
+            double va[kPIpt];
+            uint32_t flags = 0, cnt = 0;
+#pragma unroll
+            for (int j = 0; j < kPIpt; ++j) {
+                const uint32_t fl = part_flags(it[j], g, t_keys, t_b, t_tag, dbits, ctl, nxt, &va[j]);
+                flags |= fl << (2 * j);
+                cnt += __popc(fl);
             }
             uint32_t tot;
-            const uint32_t off = block_exclusive_scan<kPBlock>(__popc(flags), &tot, s_scan);
-            if (threadIdx.x == 0)
-                s_base = tot ? atomicAdd(&ctl->count[cur ^ 1], (unsigned long long)tot) : 0ULL;
-            __syncthreads();
+            const uint32_t off = scan_one_barrier<kPBlock>(cnt, s_warp, &tot);   // (2)
+            if (threadIdx.x == 0) {
+                const unsigned long long base =
+                    tot ? atomicAdd(&ctl->count[nxt], (unsigned long long)tot) : 0ULL;
+                s_base = base;
+                dout[p].off = base;
+                dout[p].cnt = tot;
+                if (tot > kSplitAt) ctl->part_over = 1;
+            }
+            __syncthreads();                                   // (3) segment claimed
             const unsigned long long base = s_base;
             if (base + tot > cap_out) {
                 if (threadIdx.x == 0) set_status(ctl, ST_CAPACITY, 2);
@@ -292,17 +482,58 @@ k_gate_part(const PKey<W>* __restrict__ pk, const double* __restrict__ pc,
             uint64_t pos = base + off;
 #pragma unroll
             for (int j = 0; j < kPIpt; ++j) {
-                if ((flags >> (2 * j)) & 1u) {
-                    store_key_stream(kout + pos, it[j].K);
-                    __stcs(cout + pos, va[j]);
-                    ++pos;
-                }
-                if ((flags >> (2 * j + 1)) & 1u) {
-                    store_key_stream(kout + pos, key_xor(it[j].K, g));
-                    __stcs(cout + pos, it[j].b);
-                    ++pos;
-                }
+                const uint32_t fl = (flags >> (2 * j)) & 3u;
+                part_write(it[j], g, va[j], fl, kout, cout, pos);
+                pos += __popc(fl);
             }
+            for (int s2 = threadIdx.x; s2 < S; s2 += kPBlock) t_tag[s2] = 0u;
+            __syncthreads();                                   // (4) next partition
+        } else {
+            // a long partition: build the table, count its output, then
+            // recompute and write (every item reloaded each pass)
+            for (uint64_t i = threadIdx.x; i < np; i += kPBlock) {
+                const PartItem<W> x = part_item(kp, cp, i, np, g, rnorm, pd, ctl);
+                if (x.comm) ok &= part_insert(x, t_keys, t_b, t_tag);
+            }
+            if (!ok) set_status(ctl, ST_CAPACITY, 41);
+            if (threadIdx.x == 0) s_total = 0u;
+            __syncthreads();
+            if (from_scatter && threadIdx.x == 0) cursor[p] = 0u;
+            for (uint64_t c0 = 0; c0 < np; c0 += kPBlock) {
+                const PartItem<W> x = part_item(kp, cp, c0 + threadIdx.x, np, g, rnorm, pd, ctl);
+                double va;
+                const uint32_t fl = part_flags(x, g, t_keys, t_b, t_tag, dbits, ctl, nxt, &va);
+                uint32_t tot;
+                block_exclusive_scan<kPBlock>(__popc(fl), &tot, s_scan);
+                if (threadIdx.x == 0) s_total += tot;
+            }
+            __syncthreads();
+            if (threadIdx.x == 0) {
+                const uint32_t tot = s_total;
+                const unsigned long long base =
+                    tot ? atomicAdd(&ctl->count[nxt], (unsigned long long)tot) : 0ULL;
+                s_base = base;
+                dout[p].off = base;
+                dout[p].cnt = tot;
+                if (tot > kSplitAt) ctl->part_over = 1;
+            }
+            __syncthreads();
+            const unsigned long long base = s_base;
+            if (base + s_total > cap_out) {
+                if (threadIdx.x == 0) set_status(ctl, ST_CAPACITY, 2);
+                return;
+            }
+            uint64_t run = 0;
+            for (uint64_t c0 = 0; c0 < np; c0 += kPBlock) {
+                const PartItem<W> x = part_item(kp, cp, c0 + threadIdx.x, np, g, rnorm, pd, ctl);
+                double va;
+                const uint32_t fl = part_flags(x, g, t_keys, t_b, t_tag, dbits, ctl, nxt, &va);
+                uint32_t tot;
+                const uint32_t off = block_exclusive_scan<kPBlock>(__popc(fl), &tot, s_scan);
+                part_write(x, g, va, fl, kout, cout, base + run + off);
+                run += tot;
+            }
+            for (int s2 = threadIdx.x; s2 < S; s2 += kPBlock) t_tag[s2] = 0u;
             __syncthreads();
         }
     }
@@ -322,26 +553,36 @@ static Bufs<W> pbufs_of(const DeviceState& s) {
 }
 
 template <int W>
-static void gate_and_pivot(const HostGate& h, GateArg<W>* g, PivotArg<W>* pv) {
-    for (int w = 0; w < W; ++w) { g->qx[w] = h.qx[w]; g->qz[w] = h.qz[w]; }
-    g->ch = h.ch;
-    g->msh = h.msh;
-    g->qyy = h.qyy;
-    pv->word = -1;
-    pv->bit = 0;
-    for (int w = 0; w < 2 * W && pv->word < 0; ++w) {
-        const uint64_t m = w < W ? h.qx[w] : h.qz[w - W];
-        if (m) { pv->word = w; pv->bit = m & (~m + 1); }
-    }
+static GateArg<W> gate_of(const HostGate& h) {
+    GateArg<W> g;
+    for (int w = 0; w < W; ++w) { g.qx[w] = h.qx[w]; g.qz[w] = h.qz[w]; }
+    g.ch = h.ch;
+    g.msh = h.msh;
+    g.qyy = h.qyy;
+    return g;
 }
 
 template <int W>
-static cudaError_t scatter_w(const DeviceState& s, const HostGate& h, cudaStream_t st) {
-    GateArg<W> g;
-    PivotArg<W> pv;
-    gate_and_pivot<W>(h, &g, &pv);
-    cudaError_t e = cudaMemsetAsync(s.part_cursor, 0, (size_t)s.part_max * sizeof(unsigned int), st);
-    if (e != cudaSuccess) return e;
+static PartFn<W> part_fn_of(const HostGate& h) {
+    PartFn<W> f;
+    for (int w = 0; w < W; ++w) { f.kx[w] = h.keep_x[w]; f.kz[w] = h.keep_z[w]; }
+    f.pair = h.pair_mode;
+    f.sites = h.win_sites;
+    f.word = -1;
+    f.bit = 0;
+    for (int w = 0; w < 2 * W && f.word < 0; ++w) {
+        const uint64_t m = w < W ? h.qx[w] : h.qz[w - W];
+        if (m) { f.word = w; f.bit = m & (~m + 1); }
+    }
+    return f;
+}
+
+template <int W>
+static cudaError_t scatter_w(const DeviceState& s, const HostGate& h, int force, cudaStream_t st) {
+    if (force) {
+        cudaError_t e = cudaMemsetAsync(s.part_cursor, 0, (size_t)s.part_max * sizeof(unsigned int), st);
+        if (e != cudaSuccess) return e;
+    }
     uint64_t gs = (s.buf_cap + 255) / 256;
     const uint64_t lim = (uint64_t)s.num_sms * 8;
     if (gs > lim) gs = lim;
@@ -349,7 +590,8 @@ static cudaError_t scatter_w(const DeviceState& s, const HostGate& h, cudaStream
     k_part_scatter<W><<<(int)gs, 256, 0, st>>>(pbufs_of<W>(s), s.ctl,
                                                reinterpret_cast<PKey<W>*>(s.part_keys),
                                                s.part_coef, s.part_cursor, s.part_cap,
-                                               s.part_max, g, pv);
+                                               s.part_max, gate_of<W>(h), part_fn_of<W>(h), force,
+                                               s.n);
     return cudaGetLastError();
 }
 
@@ -360,21 +602,23 @@ static cudaError_t merge_wbi(const DeviceState& s, const GateArg<W>& g, cudaStre
         cudaFuncSetAttribute(k_gate_part<W, BLOCK, IPT>,
                              cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)part_smem_bytes<W>());
+        // shared memory for every resident CTA's table rather than L1
+        cudaFuncSetAttribute(k_gate_part<W, BLOCK, IPT>,
+                             cudaFuncAttributePreferredSharedMemoryCarveout,
+                             (int)cudaSharedmemCarveoutMaxShared);
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_gate_part<W, BLOCK, IPT>, BLOCK,
                                                       part_smem_bytes<W>());
         if (per_sm < 1) per_sm = 1;
     }
     k_gate_part<W, BLOCK, IPT><<<s.num_sms * per_sm, BLOCK, part_smem_bytes<W>(), st>>>(
-        reinterpret_cast<const PKey<W>*>(s.part_keys), s.part_coef, s.part_cursor,
-        pbufs_of<W>(s), s.ctl, s.part_cap, s.part_max, g, s.delta, s.buf_cap);
+        reinterpret_cast<const PKey<W>*>(s.part_keys), s.part_coef, s.part_cursor, s.part_cap,
+        s.part_desc[0], s.part_desc[1], pbufs_of<W>(s), s.ctl, g, s.delta, s.buf_cap);
     return cudaGetLastError();
 }
 
 template <int W>
 static cudaError_t merge_w(const DeviceState& s, const HostGate& h, cudaStream_t st) {
-    GateArg<W> g;
-    PivotArg<W> pv;
-    gate_and_pivot<W>(h, &g, &pv);
+    const GateArg<W> g = gate_of<W>(h);
     switch (s.block * 16 + s.ipt) {
         case 128 * 16 + 1: return merge_wbi<W, 128, 1>(s, g, st);
         case 128 * 16 + 2: return merge_wbi<W, 128, 2>(s, g, st);
@@ -389,12 +633,50 @@ static cudaError_t merge_w(const DeviceState& s, const HostGate& h, cudaStream_t
     }
 }
 
-cudaError_t launch_part_scatter(const DeviceState& s, const HostGate& h, cudaStream_t st) {
-    return s.W == 1 ? scatter_w<1>(s, h, st) : scatter_w<2>(s, h, st);
+cudaError_t launch_part_scatter(const DeviceState& s, const HostGate& h, int force,
+                                cudaStream_t st) {
+    return s.W == 1 ? scatter_w<1>(s, h, force, st) : scatter_w<2>(s, h, force, st);
 }
 
 cudaError_t launch_part_merge(const DeviceState& s, const HostGate& h, cudaStream_t st) {
     return s.W == 1 ? merge_w<1>(s, h, st) : merge_w<2>(s, h, st);
+}
+
+void plan_windows(int W, std::vector<HostGate>& gates) {
+    const int max_sites = W == 1 ? PartGeom<1>::kWinSites : PartGeom<2>::kWinSites;
+    auto sites = [](const uint64_t* m) {
+        return __builtin_popcountll(m[0]) + __builtin_popcountll(m[1]);
+    };
+    size_t k = 0;
+    while (k < gates.size()) {
+        uint64_t S[2] = {gates[k].qx[0] | gates[k].qz[0], gates[k].qx[1] | gates[k].qz[1]};
+        if (sites(S) > max_sites) {
+            // a wide gate: a window of its own, partitioned by its pair key
+            HostGate& h = gates[k];
+            h.pair_mode = 1;
+            h.win_start = 1;
+            for (int w = 0; w < 2; ++w) { h.keep_x[w] = ~0ULL; h.keep_z[w] = ~0ULL; }
+            ++k;
+            continue;
+        }
+        size_t e = k + 1;
+        while (e < gates.size()) {
+            const uint64_t T[2] = {S[0] | gates[e].qx[0] | gates[e].qz[0],
+                                   S[1] | gates[e].qx[1] | gates[e].qz[1]};
+            if (sites(T) > max_sites) break;
+            S[0] = T[0];
+            S[1] = T[1];
+            ++e;
+        }
+        for (size_t j = k; j < e; ++j) {
+            HostGate& h = gates[j];
+            h.pair_mode = 0;
+            h.win_sites = sites(S);
+            h.win_start = j == k;
+            for (int w = 0; w < 2; ++w) { h.keep_x[w] = ~S[w]; h.keep_z[w] = ~S[w]; }
+        }
+        k = e;
+    }
 }
 
 uint32_t partition_max(int W, uint64_t cap_M) {

@@ -261,6 +261,31 @@ def test_launch_shapes_give_identical_states(block, ipt, load):
     assert_same_state(g.terms(), o.terms(), f"block={block} ipt={ipt} load={load}")
 
 
+@pytest.mark.parametrize("n,cap_policy,delta", [(10, 0, 1e-7), (12, 1, 1e-7), (70, 0, 1e-3)])
+@pytest.mark.parametrize("block,ipt", [(128, 1), (512, 2)])
+def test_partitioned_merge_windows_and_long_partitions(n, cap_policy, delta, block, ipt):
+    # 128 x 1 holds 128 items in registers: every partition takes the
+    # two-pass path and every gate's output re-partitions (split limit 256),
+    # exercising the conditional scatter inside a window
+    H = wl.tfim_1d(n, 1.0, 0.9, periodic=True)
+    cap = 3000 if cap_policy else 1 << 20
+    g, o = _pair(H, 0.1, delta, cap_M=cap, cap_policy=cap_policy, block_threads=block,
+                 items_per_thread=ipt, merge_path=0)
+    for layer in range(3):
+        g.apply_trotter_layer(1)
+        o.apply_layers(1)
+        assert_same_state(g.terms(), o.terms(), f"{block}x{ipt} layer {layer}")
+    g.apply_gate(3)                  # a single gate: a window of its own
+    o.apply_gate(3)
+    g.apply_gate(4)                  # the next gate reuses no stale partition
+    o.apply_gate(4)
+    assert_same_state(g.terms(), o.terms(), "single gates")
+    st = g.stats()
+    assert st["repartitions"] >= 3 * 2     # at least one scatter per bond / field window
+    if block == 128:                        # every output past the split limit
+        assert st["repartitions"] >= 3 * H.n_gates // 2
+
+
 @pytest.mark.parametrize("n,W_delta", [(64, 1e-4), (100, 2e-4)])
 def test_merge_paths_identical(n, W_delta):
     # partitioned shared-memory merge vs one global table, many partitions
