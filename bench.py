@@ -525,6 +525,8 @@ def main():
             "timed_gates": int(gates),
             "table_probes_per_term": (st1["table_probes"] - st0["table_probes"]) / max(terms_in, 1),
             "repartitions_per_gate": (st1["repartitions"] - st0["repartitions"]) / max(gates, 1),
+            "select_candidates_per_gate": (st1["select_candidates"] - st0["select_candidates"]) / max(gates, 1),
+            "select_range_bits": int(st1["select_range"]).bit_length(),
             "terms_in_timed": int(terms_in),
         }
         print(json.dumps(line), flush=True)

@@ -107,6 +107,10 @@ typedef struct {
     uint64_t kernel_launches; /* kernels this handle has launched (host count)  */
     uint64_t repartitions;    /* partitioned merge: scatters run (window starts,
                                * state changes, partitions past the split limit) */
+    uint64_t select_candidates; /* top-M selects: terms in the threshold's first
+                                 * digit, summed over gates                      */
+    uint64_t select_range;    /* last top-M select: largest |c| pattern minus the
+                               * threshold's pattern (the first digit's range)   */
 } itpp_stats;
 
 /* ---------------------------------------------------------------------------

@@ -41,7 +41,8 @@ class itpp_stats(ctypes.Structure):
                 ("terms_out", ctypes.c_uint64), ("peak_terms", ctypes.c_uint64),
                 ("cap_events", ctypes.c_uint64), ("count", ctypes.c_uint64),
                 ("table_probes", ctypes.c_uint64), ("kernel_launches", ctypes.c_uint64),
-                ("repartitions", ctypes.c_uint64)]
+                ("repartitions", ctypes.c_uint64), ("select_candidates", ctypes.c_uint64),
+                ("select_range", ctypes.c_uint64)]
 
 
 class ItppError(RuntimeError):

@@ -196,6 +196,8 @@ __global__ void k_import_begin(DevCtl* ctl, uint64_t count) {
         ctl->sel_tie_n = 0;
         ctl->stat_gates = ctl->stat_in = ctl->stat_out = ctl->stat_cap = ctl->stat_probes = 0;
         ctl->stat_scatters = 0;
+        ctl->stat_cands = 0;
+        ctl->stat_range = 0;
         ctl->stat_peak = count;
         ctl->sel_k = 0;   // reused below as "identity seen" flag
         ctl->pend = 0;
@@ -331,6 +333,8 @@ __global__ void k_reset_identity(BufsA<W> B, DevCtl* ctl) {
         ctl->pend = 0;
         ctl->stat_gates = ctl->stat_in = ctl->stat_out = ctl->stat_cap = ctl->stat_probes = 0;
         ctl->stat_scatters = 0;
+        ctl->stat_cands = 0;
+        ctl->stat_range = 0;
         ctl->stat_peak = 1;
     }
 }

@@ -301,6 +301,8 @@ itpp_status itpp_batch_get_stats(itpp_batch_handle h, int b, itpp_stats* o) {
     o->count = c->count[c->cur];
     o->table_probes = c->stat_probes;
     o->repartitions = 0;
+    o->select_candidates = 0;
+    o->select_range = 0;
     o->kernel_launches = h->launches;
     return (itpp_status)c->status;
 }

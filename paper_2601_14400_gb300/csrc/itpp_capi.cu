@@ -411,6 +411,8 @@ itpp_status itpp_get_stats(itpp_handle h, itpp_stats* o) {
     o->count = c.count[c.cur];
     o->table_probes = c.stat_probes;
     o->repartitions = c.stat_scatters;
+    o->select_candidates = c.stat_cands;
+    o->select_range = c.stat_range;
     o->kernel_launches = h->launches;
     return st;
 }

@@ -74,6 +74,7 @@ struct DevCtl {
     unsigned long long stat_gates, stat_in, stat_out, stat_peak, stat_cap;
     unsigned long long stat_probes;
     unsigned long long stat_scatters;
+    unsigned long long stat_cands, stat_range;
     // top-M select state
     int sel_active;
     int sel_pass;
@@ -101,6 +102,11 @@ struct DevCtl {
     int part_from_scatter;           // 1: in the scatter buffer; 0: segments of the state
     int part_over;                   // this gate left a partition above the split limit
     int need_scatter;                // ... so the next gate re-partitions
+    // top-M select geometry: largest |c| pattern the gate wrote (partitioned
+    // merge), the value the select uses, and the last-CTA counter
+    unsigned long long out_max;
+    unsigned long long sel_hi;
+    unsigned int sel_done;
     unsigned long long sel_hist[kSelBins];
     unsigned long long tie_hist[kTieBins];
 };

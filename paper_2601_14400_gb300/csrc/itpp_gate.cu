@@ -217,103 +217,6 @@ __global__ void k_cap_end(DevCtl* ctl) {
     }
 }
 
-// ---------------------------------------------------------------------------
-// Top-M select with a candidate list and a deferred compaction (the
-// partitioned merge).  After the first 13-bit digit only the terms in the
-// threshold's bucket can matter: they are gathered once (value bits and
-// index) and the remaining digits, and the tie list, are taken over that
-// list.  The kept set is then left as a predicate (threshold, tie key) that
-// the next gate's scatter applies as it reads the state, or that an
-// explicit materialisation applies before the state is read otherwise.
-// ---------------------------------------------------------------------------
-template <int W, int BLOCK>
-__global__ void __launch_bounds__(BLOCK)
-k_cap_gather(Bufs<W> B, DevCtl* ctl, unsigned long long* cand_bits, uint32_t* cand_idx) {
-    if (!ctl->sel_active || ctl->status) return;
-    __shared__ uint32_t s_scan[BLOCK / 32];
-    __shared__ unsigned long long s_base;
-    const int cur = ctl->cur;
-    const uint64_t n = live_count(ctl, cur);
-    const unsigned long long prefix = ctl->sel_prefix, mask = ctl->sel_mask;
-    const double* __restrict__ c = B.c[cur];
-    const uint64_t tiles = (n + BLOCK - 1) / BLOCK;
-    for (uint64_t t = blockIdx.x; t < tiles; t += gridDim.x) {
-        const uint64_t i = t * BLOCK + threadIdx.x;
-        unsigned long long b = 0;
-        bool in = false;
-        if (i < n) {
-            b = abs_bits(__ldcs(c + i));
-            in = (b & mask) == prefix;
-        }
-        uint32_t tot;
-        const uint32_t off = block_exclusive_scan<BLOCK>(in ? 1u : 0u, &tot, s_scan);
-        if (threadIdx.x == 0)
-            s_base = tot ? atomicAdd(&ctl->sel_cand_n, (unsigned long long)tot) : 0ULL;
-        __syncthreads();
-        if (in) {
-            cand_bits[s_base + off] = b;
-            cand_idx[s_base + off] = (uint32_t)i;
-        }
-    }
-}
-
-__global__ void __launch_bounds__(256)
-k_cand_hist(DevCtl* ctl, const unsigned long long* cand_bits, int shift) {
-    if (!ctl->sel_active || ctl->status) return;
-    __shared__ unsigned int h[kSelBins];
-    for (int b = threadIdx.x; b < kSelBins; b += blockDim.x) h[b] = 0;
-    __syncthreads();
-    const unsigned long long n = ctl->sel_cand_n;
-    const unsigned long long prefix = ctl->sel_prefix, mask = ctl->sel_mask;
-    for (unsigned long long i = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x; i < n;
-         i += (unsigned long long)gridDim.x * blockDim.x) {
-        const unsigned long long b = cand_bits[i];
-        if ((b & mask) == prefix) atomicAdd(&h[(b >> shift) & (kSelBins - 1)], 1u);
-    }
-    __syncthreads();
-    for (int b = threadIdx.x; b < kSelBins; b += blockDim.x)
-        if (h[b]) atomicAdd(&ctl->sel_hist[b], (unsigned long long)h[b]);
-}
-
-// Keys of the candidates exactly at the threshold (when some are dropped).
-template <int W, int BLOCK>
-__global__ void __launch_bounds__(BLOCK)
-k_cand_ties(Bufs<W> B, DevCtl* ctl, const unsigned long long* cand_bits, const uint32_t* cand_idx,
-            PKey<W>* tie_list) {
-    if (!tie_select_needed(ctl)) return;
-    __shared__ uint32_t s_scan[BLOCK / 32];
-    __shared__ unsigned long long s_base;
-    const int cur = ctl->cur;
-    const unsigned long long n = ctl->sel_cand_n;
-    const unsigned long long T = ctl->sel_prefix;
-    const uint64_t tiles = (n + BLOCK - 1) / BLOCK;
-    for (uint64_t t = blockIdx.x; t < tiles; t += gridDim.x) {
-        const uint64_t j = t * BLOCK + threadIdx.x;
-        const bool tie = j < n && cand_bits[j] == T;
-        uint32_t tot;
-        const uint32_t off = block_exclusive_scan<BLOCK>(tie ? 1u : 0u, &tot, s_scan);
-        if (threadIdx.x == 0)
-            s_base = tot ? atomicAdd(&ctl->sel_tie_n, (unsigned long long)tot) : 0ULL;
-        __syncthreads();
-        if (tie) tie_list[s_base + off] = load_key(B.k[cur] + cand_idx[j]);
-    }
-}
-
-// Leave the kept set as a predicate on the current buffer.
-__global__ void k_cap_defer(DevCtl* ctl, uint64_t cap_M) {
-    if (threadIdx.x != 0 || !ctl->sel_active) return;
-    if (!ctl->status) {
-        const int cur = ctl->cur;
-        ctl->pend = 1;
-        ctl->pend_n = ctl->count[cur];
-        ctl->pend_T = ctl->sel_prefix;
-        ctl->pend_all_ties = ctl->sel_k == ctl->sel_ties;
-        for (int w = 0; w < 4; ++w) ctl->pend_tie_key[w] = ctl->sel_tie_key[w];
-        ctl->count[cur] = cap_M;   // the logical term count
-    }
-    ctl->sel_active = 0;
-}
-
 template <int W>
 __device__ __forceinline__ PKey<W> pend_tie_key(const DevCtl* ctl) {
     PKey<W> tk;
@@ -473,34 +376,7 @@ cudaError_t launch_cap_select(const DeviceState& s, cudaStream_t st) {
 }
 
 int cap_launches(const DeviceState& s) {
-    return s.merge_deferred ? 2 + 1 + 4 * 2 + 1 + 8 * s.W * 2 + 2 : 5 * 2 + 1 + 8 * s.W * 2 + 3;
-}
-
-template <int W>
-static cudaError_t cap_deferred_w(const DeviceState& s, cudaStream_t st) {
-    const int g = stream_grid(s, 256, 8);
-    k_cap_hist<W><<<g, 256, 0, st>>>(bufs_of<W>(s), s.ctl, 50);
-    k_cap_pick<<<1, 1024, 0, st>>>(s.ctl, 50, 0);
-    // candidates and tie keys live in the merge table's memory (free after
-    // the merge): at least 32 bytes per buffer slot, here 12 + 16W are used
-    char* scratch = static_cast<char*>(s.table);
-    unsigned long long* cand_bits = reinterpret_cast<unsigned long long*>(scratch);
-    uint32_t* cand_idx = reinterpret_cast<uint32_t*>(cand_bits + s.buf_cap);
-    PKey<W>* ties = reinterpret_cast<PKey<W>*>(scratch + (s.buf_cap * 12 + 255) / 256 * 256);
-    k_cap_gather<W, 256><<<g, 256, 0, st>>>(bufs_of<W>(s), s.ctl, cand_bits, cand_idx);
-    const int shifts[4] = {37, 24, 11, 0};
-    for (int p = 0; p < 4; ++p) {
-        k_cand_hist<<<g, 256, 0, st>>>(s.ctl, cand_bits, shifts[p]);
-        k_cap_pick<<<1, 1024, 0, st>>>(s.ctl, shifts[p], p == 3 ? 1 : 0);
-    }
-    k_cand_ties<W, 256><<<g, 256, 0, st>>>(bufs_of<W>(s), s.ctl, cand_bits, cand_idx, ties);
-    for (int p = 0; p < 8 * W; ++p) {
-        k_tie_hist<W><<<g, 256, 0, st>>>(s.ctl, ties, p);
-        k_tie_pick<W><<<1, 1024, 0, st>>>(s.ctl, p);
-    }
-    k_tie_find<W><<<g, 256, 0, st>>>(s.ctl, ties);
-    k_cap_defer<<<1, 32, 0, st>>>(s.ctl, s.cap_M);
-    return cudaGetLastError();
+    return s.merge_deferred ? 3 : 5 * 2 + 1 + 8 * s.W * 2 + 3;
 }
 
 template <int W>
@@ -517,7 +393,7 @@ cudaError_t launch_materialize(const DeviceState& s, cudaStream_t st) {
 }
 
 cudaError_t launch_cap(const DeviceState& s, cudaStream_t st) {
-    if (s.merge_deferred) return s.W == 1 ? cap_deferred_w<1>(s, st) : cap_deferred_w<2>(s, st);
+    if (s.merge_deferred) return launch_select_deferred(s, st);
     return s.W == 1 ? cap_w<1>(s, st) : cap_w<2>(s, st);
 }
 

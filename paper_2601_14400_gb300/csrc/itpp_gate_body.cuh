@@ -250,6 +250,8 @@ __device__ __forceinline__ int post_one(DevCtl* ctl, uint64_t cap_M, int cap_pol
     ctl->pend = 0;   // a deferred select was applied by this gate's scatter or merge
     ctl->need_scatter = ctl->part_over;
     ctl->part_over = 0;
+    ctl->sel_hi = ctl->out_max;
+    ctl->out_max = 0;
     const int cur = ctl->cur, nxt = cur ^ 1;
     const unsigned long long n_in = ctl->count[cur], n_out = ctl->count[nxt];
     ctl->cur = nxt;

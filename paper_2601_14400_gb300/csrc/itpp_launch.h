@@ -77,6 +77,9 @@ int cap_launches(const DeviceState& s);
 // The select part only (threshold and tie key in the control block, no
 // compaction): used where the kept set is compacted elsewhere.
 cudaError_t launch_cap_select(const DeviceState& s, cudaStream_t st);
+// The top-M select of the partitioned merge (itpp_select.cu): leaves the
+// kept set as a predicate for the next gate's reads.
+cudaError_t launch_select_deferred(const DeviceState& s, cudaStream_t st);
 // Apply a deferred top-M select (compaction); a no-op when none is pending.
 cudaError_t launch_materialize(const DeviceState& s, cudaStream_t st);
 // Sort-based merge path (children buffer, radix sort, segmented reduce).

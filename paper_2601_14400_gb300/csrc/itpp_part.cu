@@ -406,6 +406,7 @@ k_gate_part(const PKey<W>* __restrict__ pk, const double* __restrict__ pc,
     const Pending<W> pd = pending_of<W>(ctl);
     PKey<W>* __restrict__ kout = B.k[nxt];
     double* __restrict__ cout = B.c[nxt];
+    unsigned long long out_max = 0;   // largest |c| pattern written (top-M select range)
     for (int s2 = threadIdx.x; s2 < S; s2 += kPBlock) t_tag[s2] = 0u;
     __syncthreads();
     for (uint32_t p = blockIdx.x; p < P; p += gridDim.x) {
@@ -485,6 +486,8 @@ k_gate_part(const PKey<W>* __restrict__ pk, const double* __restrict__ pc,
                 const uint32_t fl = (flags >> (2 * j)) & 3u;
                 part_write(it[j], g, va[j], fl, kout, cout, pos);
                 pos += __popc(fl);
+                out_max = max(out_max, (fl & 1u) ? abs_pattern(va[j]) : 0ULL);
+                out_max = max(out_max, (fl & 2u) ? abs_pattern(it[j].b) : 0ULL);
             }
             for (int s2 = threadIdx.x; s2 < S; s2 += kPBlock) t_tag[s2] = 0u;
             __syncthreads();                                   // (4) next partition
@@ -531,12 +534,18 @@ k_gate_part(const PKey<W>* __restrict__ pk, const double* __restrict__ pc,
                 uint32_t tot;
                 const uint32_t off = block_exclusive_scan<kPBlock>(__popc(fl), &tot, s_scan);
                 part_write(x, g, va, fl, kout, cout, base + run + off);
+                out_max = max(out_max, (fl & 1u) ? abs_pattern(va) : 0ULL);
+                out_max = max(out_max, (fl & 2u) ? abs_pattern(x.b) : 0ULL);
                 run += tot;
             }
             for (int s2 = threadIdx.x; s2 < S; s2 += kPBlock) t_tag[s2] = 0u;
             __syncthreads();
         }
     }
+    // one atomic per warp for the largest pattern
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) out_max = max(out_max, __shfl_xor_sync(0xffffffffu, out_max, o));
+    if ((threadIdx.x & 31) == 0 && out_max) atomicMax(&ctl->out_max, out_max);
 }
 
 // ---------------------------------------------------------------------------
