@@ -70,10 +70,12 @@ def parse():
     ap.add_argument("--merge-path", type=int, default=0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
-    ap.add_argument("--mode", default="headline", choices=["headline", "batch", "adjoint"],
+    ap.add_argument("--mode", default="headline", choices=["headline", "batch", "adjoint", "synth"],
                     help="headline: the metric line; batch / adjoint: the extension "
                          "timings against plain single-instance runs")
     ap.add_argument("--batch-cap-log2", type=int, default=16)
+    ap.add_argument("--synth-sizes", default="20,23,26",
+                    help="log2 of the synthetic state sizes (--mode synth)")
     ap.add_argument("--adjoint-layers", type=int, default=50)
     ap.add_argument("--adjoint-ckpt", type=int, default=10)
     ap.add_argument("--batch-layers", type=int, default=5)
@@ -247,7 +249,8 @@ def run_batch(args):
     stream = torch.cuda.Stream()
     # batched
     bp = itpp.BatchPropagator(hams, dtau, delta, M, cap_policy=1, stream=stream)
-    bp.apply_trotter_layer(0)
+    # launch shapes and table load from the autotuner, timed on these layers
+    tune = bp.autotune(probe_layers=L)
     torch.cuda.synchronize()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e0.record(stream)
@@ -279,11 +282,69 @@ def run_batch(args):
             "value": terms_b / (t_batch * 1e-3), "unit": UNIT,
             "plain_value": terms_p / (t_plain * 1e-3), "speedup": t_plain / t_batch,
             "batched_ms": t_batch, "plain_ms": t_plain, "identical_results": bool(same),
+            "autotune": tune,
             "config": {"workload": "field sweep: 64 open TFIM chains, n~U{16..64}, "
                                    "h~U[0.5,2], J=1", "dtau": dtau, "delta": delta,
                        "cap_M": M, "cap_policy": "top-M", "layers": L,
                        "terms_final": int(sum(counts_b))},
             "dtype": "f64", "data": "synthetic"}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def run_synth(args):
+    """One gate (Q = Z_10 Z_11 and Q = X_10, separately) on seeded synthetic
+    states of M random TFIM-sector strings (sign uniform, |c| log-uniform in
+    [delta, 1], seed 2601) at n = 64 (W = 1) and n = 121 (W = 2): the roofline
+    sweep of the propagate-merge-truncate step.  Each point: the state is
+    imported (untimed), then one gate is timed with CUDA events on the
+    library stream; best of three."""
+    import torch
+    import paper_2601_14400_gb300 as itpp
+    if not os.path.exists(itpp.LIB_PATH):
+        itpp.build()
+    peak, peak_kind = load_peaks()
+    stream = torch.cuda.Stream()
+    delta, dtau = 1e-6, 0.01
+    logs = [int(v) for v in args.synth_sizes.split(",")]
+    points = []
+    for n in (64, 121):
+        W = wl.n_words(n)
+        for lm in logs:
+            M = 1 << lm
+            X, Z, C = wl.synthetic_state(n, M, 2601, delta)
+            for kind in ("ZZ", "X"):
+                gx, gz = (wl.two_site(n, 10, 11, "Z", "Z") if kind == "ZZ"
+                          else wl.single_site(n, 10, "X"))
+                H = wl.Hamiltonian(n, gx[None], gz[None], np.array([-1.0]))
+                g = itpp.Propagator(n, H.gate_x, H.gate_z, H.alpha, dtau, delta, 2 * M + 2, 0,
+                                    stream=stream)
+                best = None
+                for _ in range(3):
+                    g.set_terms(X, Z, C)
+                    g.synchronize()
+                    e0 = torch.cuda.Event(enable_timing=True)
+                    e1 = torch.cuda.Event(enable_timing=True)
+                    e0.record(stream)
+                    g.apply_gate(0)
+                    e1.record(stream)
+                    g.synchronize()
+                    ms = e0.elapsed_time(e1)
+                    best = ms if best is None else min(best, ms)
+                n_in, n_out = M + 1, g.count()
+                b_alg = (n_in + n_out) * (16 * W + 8)
+                points.append({"n": n, "W": W, "M": M, "gate": kind, "ms": best,
+                               "terms_per_s": n_in / (best * 1e-3), "n_out": n_out,
+                               "alg_gb_s": b_alg / (best * 1e-3) / 1e9,
+                               "frac": b_alg / (best * 1e-3) / 1e9 / peak})
+                g.close()
+                torch.cuda.synchronize()
+            del X, Z, C
+    line = {"metric": "synthetic roofline sweep: one gate, propagate-merge-truncate",
+            "mode": "synth", "unit": "terms/s", "peak_gb_s": peak, "peak_source": peak_kind,
+            "points": points, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": "synthetic TFIM-sector states, seed 2601", "delta": delta,
+                       "dtau": dtau, "gates": "Z10Z11 and X10", "best_of": 3}}
     print(json.dumps(line), flush=True)
     return 0
 
@@ -372,6 +433,8 @@ def main():
         return run_batch(args)
     if args.mode == "adjoint":
         return run_adjoint(args)
+    if args.mode == "synth":
+        return run_synth(args)
     w = wl.WORKLOADS[args.workload]
     if args.cap_log2:
         w.cap_M = 1 << args.cap_log2

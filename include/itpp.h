@@ -294,6 +294,32 @@ itpp_status itpp_batch_apply_trotter_layer(itpp_batch_handle h, int n_layers);
 /* Wait; ITPP_OK if every instance is healthy, else the first error. */
 itpp_status itpp_batch_synchronize(itpp_batch_handle h);
 
+/* The launch shape and hash sizing of a batch, chosen by timing (the
+ * autotuner of the batched path).  Tuned: threads per CTA of the
+ * branch-emit kernel (128, 256, 512; two terms per thread), its CTAs per SM
+ * (2, 4, 8), the table build's CTAs per SM (4, 8, 16) and the merge table's
+ * highest load (25..65 %; itpp_batch_create with table_load_pct 0 sizes the
+ * tables for 25 %, otherwise loads below the requested one are not tried).
+ * Each candidate is timed with CUDA events over probe_layers Trotter layers
+ * from the identity, replayed as the layer graph; coordinate descent from
+ * the default shape, one parameter at a time.  The fastest shape stays
+ * installed.  Every instance is reset to the identity before each timing
+ * and after the search (statistics cleared), so results never depend on the
+ * tuning: every shape gives bit-identical states.  Synchronising.
+ *   probe_layers  >= 1.
+ *   out           host, may be NULL. */
+typedef struct {
+    int main_block;              /* threads per CTA of the branch-emit kernel   */
+    int main_grid;               /* its CTAs per SM                              */
+    int insert_grid;             /* CTAs per SM of the table build               */
+    int table_load_pct;          /* highest load of every instance's table (%)   */
+    double ms_per_probe;         /* the chosen shape: probe_layers layers (ms)   */
+    double ms_per_probe_default; /* the default shape (256, 4, 8, 50 %)          */
+    int candidates;              /* shapes timed                                 */
+    int reserved[3];
+} itpp_tune_result;
+itpp_status itpp_batch_autotune(itpp_batch_handle h, int probe_layers, itpp_tune_result* out);
+
 /* Term count (and, when statuses != NULL, the status) of every instance;
  * host arrays of B entries.  Synchronising. */
 itpp_status itpp_batch_get_counts(itpp_batch_handle h, uint64_t* counts, int* statuses);

@@ -54,6 +54,13 @@ class ItppError(RuntimeError):
 _lib = None
 
 # (name, restype, argtypes) of every exported function of include/itpp.h
+class itpp_tune_result(ctypes.Structure):
+    _fields_ = [("main_block", ctypes.c_int), ("main_grid", ctypes.c_int),
+                ("insert_grid", ctypes.c_int), ("table_load_pct", ctypes.c_int),
+                ("ms_per_probe", ctypes.c_double), ("ms_per_probe_default", ctypes.c_double),
+                ("candidates", ctypes.c_int), ("reserved", ctypes.c_int * 3)]
+
+
 _SIGNATURES = [
     ("itpp_create", ctypes.c_int, [ctypes.c_int, _u64p, _u64p, _f64p, ctypes.c_int,
                                    ctypes.c_double, ctypes.POINTER(itpp_params), _vp,
@@ -82,6 +89,7 @@ _SIGNATURES = [
     ("itpp_batch_destroy", ctypes.c_int, [_vp]),
     ("itpp_batch_apply_trotter_layer", ctypes.c_int, [_vp, ctypes.c_int]),
     ("itpp_batch_synchronize", ctypes.c_int, [_vp]),
+    ("itpp_batch_autotune", ctypes.c_int, [_vp, ctypes.c_int, ctypes.POINTER(itpp_tune_result)]),
     ("itpp_batch_get_counts", ctypes.c_int, [_vp, _u64p, _i32p]),
     ("itpp_batch_get_stats", ctypes.c_int, [_vp, ctypes.c_int, ctypes.POINTER(itpp_stats)]),
     ("itpp_batch_get_terms", ctypes.c_int, [_vp, ctypes.c_int, _u64p, _u64p, _f64p,
@@ -344,6 +352,14 @@ class BatchPropagator:
             self.close()
         except Exception:
             pass
+
+    def autotune(self, probe_layers=2):
+        """Time launch shapes and table loads on this batch, keep the fastest
+        (every instance is reset to the identity).  Returns the choice."""
+        r = itpp_tune_result()
+        _check(lib().itpp_batch_autotune(self._h, int(probe_layers), ctypes.byref(r)),
+               "itpp_batch_autotune")
+        return {k: getattr(r, k) for k, _ in itpp_tune_result._fields_ if k != "reserved"}
 
     def apply_trotter_layer(self, n_layers=1):
         _check(lib().itpp_batch_apply_trotter_layer(self._h, int(n_layers)),

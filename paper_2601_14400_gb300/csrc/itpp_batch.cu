@@ -19,9 +19,7 @@ namespace itpp {
 
 namespace {
 
-constexpr int kBlock = 256;
-constexpr int kIpt = 2;
-constexpr uint64_t kTile = (uint64_t)kBlock * kIpt;   // branch-emit tile
+constexpr int kIpt = 2;                               // branch-emit items per thread
 constexpr uint64_t kTileH = 4096;                     // histogram tile
 constexpr uint64_t kTileC = 256;                      // compaction tile
 
@@ -78,7 +76,7 @@ __device__ __forceinline__ int owner(const unsigned long long* prefix, int B,
 
 // Plan of step `step`: which instances take a gate, their items and tiles.
 template <int W>
-__global__ void __launch_bounds__(1024) k_b_plan(BatchBufs<W> S, int step) {
+__global__ void __launch_bounds__(1024) k_b_plan(BatchBufs<W> S, int step, uint64_t kTile) {
     __shared__ unsigned long long s_part[1024];
     for (int b = threadIdx.x; b < S.B; b += blockDim.x) {
         DevCtl* ctl = S.ctl + b;
@@ -130,7 +128,7 @@ k_b_insert(BatchBufs<W> S, int step, int load_pct, int probe_limit) {
     (void)probes;
 }
 
-template <int W>
+template <int W, int kBlock>
 __global__ void __launch_bounds__(kBlock)
 k_b_main(BatchBufs<W> S, int step, double delta, int load_pct, int probe_limit) {
     __shared__ uint32_t s_scan[kBlock / 32];
@@ -340,9 +338,14 @@ template <int W>
 static cudaError_t batch_step_w(const BatchState& s, int step, cudaStream_t st) {
     const BatchBufs<W> S = batch_bufs<W>(s);
     const int grid = s.num_sms * 8;
-    k_b_plan<W><<<1, 1024, 0, st>>>(S, step);
-    k_b_insert<W><<<grid, 256, 0, st>>>(S, step, s.load_pct, s.probe_limit);
-    k_b_main<W><<<s.num_sms * 4, kBlock, 0, st>>>(S, step, s.delta, s.load_pct, s.probe_limit);
+    k_b_plan<W><<<1, 1024, 0, st>>>(S, step, (uint64_t)s.main_block * kIpt);
+    k_b_insert<W><<<s.num_sms * s.insert_grid, 256, 0, st>>>(S, step, s.load_pct, s.probe_limit);
+    const int gm = s.num_sms * s.main_grid;
+    switch (s.main_block) {
+        case 128: k_b_main<W, 128><<<gm, 128, 0, st>>>(S, step, s.delta, s.load_pct, s.probe_limit); break;
+        case 512: k_b_main<W, 512><<<gm, 512, 0, st>>>(S, step, s.delta, s.load_pct, s.probe_limit); break;
+        default:  k_b_main<W, 256><<<gm, 256, 0, st>>>(S, step, s.delta, s.load_pct, s.probe_limit); break;
+    }
     k_b_post<W><<<1, 1024, 0, st>>>(S, s.cap_M, s.cap_policy);
     if (s.cap_policy == 1) {
         const int shifts[5] = {50, 37, 24, 11, 0};

@@ -25,6 +25,7 @@ struct itpp_batch_ctx {
     size_t obs_bytes = 0;
     uint64_t launches = 0;
     std::vector<unsigned char> h_ctl;   // one DevCtl head, for reads
+    int load_floor = 50;                // lowest table load the allocation allows
 };
 
 namespace {
@@ -115,6 +116,60 @@ itpp_status read_head(itpp_batch_ctx* h, int b, DevCtl* out) {
     return ITPP_OK;
 }
 
+// Reset every instance to the identity (statistics cleared).
+itpp_status reset_all(itpp_batch_ctx* h) {
+    for (int b = 0; b < h->s.B; ++b)
+        if (launch_reset_identity(view(h, b), h->stream) != cudaSuccess) return ITPP_ERR_CUDA;
+    return ITPP_OK;
+}
+
+// Capture one Trotter layer (every gate step, all instances per launch) as
+// the handle's graph, if it has none.
+itpp_status capture_layer(itpp_batch_ctx* h) {
+    if (h->layer) return ITPP_OK;
+    cudaGraph_t g = nullptr;
+    if (cudaStreamBeginCapture(h->stream, cudaStreamCaptureModeThreadLocal) != cudaSuccess)
+        return ITPP_ERR_CUDA;
+    cudaError_t e = cudaSuccess;
+    for (int step = 0; step < h->s.max_gates && e == cudaSuccess; ++step)
+        e = launch_batch_step(h->s, step, h->stream);
+    cudaError_t e2 = cudaStreamEndCapture(h->stream, &g);
+    if (e != cudaSuccess || e2 != cudaSuccess || !g) {
+        if (g) cudaGraphDestroy(g);
+        cudaGetLastError();
+        return ITPP_ERR_CUDA;
+    }
+    e = cudaGraphInstantiate(&h->layer, g, 0);
+    cudaGraphDestroy(g);
+    return e == cudaSuccess ? ITPP_OK : ITPP_ERR_CUDA;
+}
+
+// Time probe_layers layers from the identity with the current shape.
+itpp_status time_shape(itpp_batch_ctx* h, int probe_layers, double* ms) {
+    if (h->layer) {
+        cudaGraphExecDestroy(h->layer);
+        h->layer = nullptr;
+    }
+    if (reset_all(h) != ITPP_OK || cudaStreamSynchronize(h->stream) != cudaSuccess)
+        return ITPP_ERR_CUDA;
+    // capture the layer graph outside the timed region
+    if (capture_layer(h) != ITPP_OK) return ITPP_ERR_CUDA;
+    cudaEvent_t a, b;
+    if (cudaEventCreate(&a) != cudaSuccess) return ITPP_ERR_CUDA;
+    if (cudaEventCreate(&b) != cudaSuccess) { cudaEventDestroy(a); return ITPP_ERR_CUDA; }
+    cudaEventRecord(a, h->stream);
+    for (int l = 0; l < probe_layers; ++l) cudaGraphLaunch(h->layer, h->stream);
+    cudaEventRecord(b, h->stream);
+    float f = 0.f;
+    const bool ok = cudaEventSynchronize(b) == cudaSuccess &&
+                    cudaEventElapsedTime(&f, a, b) == cudaSuccess;
+    cudaEventDestroy(a);
+    cudaEventDestroy(b);
+    if (!ok) return ITPP_ERR_CUDA;
+    *ms = f;
+    return ITPP_OK;
+}
+
 }  // namespace
 
 extern "C" {
@@ -168,7 +223,9 @@ itpp_status itpp_batch_create(int B, const int* n, const int* n_gates, const uin
     s.delta = p->delta + 0.0;   // -0 becomes +0 (the threshold compares bit patterns)
     s.load_pct = p->table_load_pct ? p->table_load_pct : 50;
     if (s.load_pct < 10 || s.load_pct > 75) { free_batch(h); delete h; return ITPP_ERR_ARG; }
-    const int load_for_size = s.load_pct < 50 ? s.load_pct : 50;
+    // auto sizing leaves room for the autotuner to try loads down to 25 %
+    const int load_for_size = p->table_load_pct ? (s.load_pct < 50 ? s.load_pct : 50) : 25;
+    h->load_floor = load_for_size;
     const uint64_t need = (p->cap_M * 100 + load_for_size - 1) / load_for_size;
     s.table_slots = next_pow2(need < 256 ? 256 : need);
     int dev = 0, sms = 1;
@@ -242,27 +299,63 @@ itpp_status itpp_batch_destroy(itpp_batch_handle h) {
 itpp_status itpp_batch_apply_trotter_layer(itpp_batch_handle h, int n_layers) {
     if (!h || n_layers < 0) return ITPP_ERR_ARG;
     if (h->sticky) return h->sticky;
-    if (!h->layer && n_layers > 0) {
-        // capture one layer: every gate step, all instances per launch
-        cudaGraph_t g = nullptr;
-        if (cudaStreamBeginCapture(h->stream, cudaStreamCaptureModeThreadLocal) != cudaSuccess)
-            return h->sticky = ITPP_ERR_CUDA;
-        cudaError_t e = cudaSuccess;
-        for (int step = 0; step < h->s.max_gates && e == cudaSuccess; ++step)
-            e = launch_batch_step(h->s, step, h->stream);
-        cudaError_t e2 = cudaStreamEndCapture(h->stream, &g);
-        if (e != cudaSuccess || e2 != cudaSuccess || !g) {
-            if (g) cudaGraphDestroy(g);
-            cudaGetLastError();
-            return h->sticky = ITPP_ERR_CUDA;
-        }
-        e = cudaGraphInstantiate(&h->layer, g, 0);
-        cudaGraphDestroy(g);
-        if (e != cudaSuccess) return h->sticky = ITPP_ERR_CUDA;
-    }
+    // one layer (every gate step, all instances per launch) as a graph
+    if (n_layers > 0 && capture_layer(h) != ITPP_OK) return h->sticky = ITPP_ERR_CUDA;
     for (int l = 0; l < n_layers; ++l) {
         if (cudaGraphLaunch(h->layer, h->stream) != cudaSuccess) return h->sticky = ITPP_ERR_CUDA;
         h->launches += (uint64_t)h->s.max_gates * batch_step_launches(h->s);
+    }
+    return ITPP_OK;
+}
+
+itpp_status itpp_batch_autotune(itpp_batch_handle h, int probe_layers, itpp_tune_result* out) {
+    if (!h || probe_layers < 1) return ITPP_ERR_ARG;
+    if (h->sticky) return h->sticky;
+    BatchState& s = h->s;
+    struct Shape { int mb, mg, ig, load; };
+    Shape best{256, 4, 8, 50 < h->load_floor ? h->load_floor : 50};
+    s.main_block = best.mb; s.main_grid = best.mg; s.insert_grid = best.ig; s.load_pct = best.load;
+    double best_ms = 0, default_ms = 0;
+    int tried = 0;
+    itpp_status st = time_shape(h, probe_layers, &best_ms);
+    if (st) return h->sticky = st;
+    default_ms = best_ms;
+    ++tried;
+    auto try_shape = [&](Shape c) -> itpp_status {
+        s.main_block = c.mb; s.main_grid = c.mg; s.insert_grid = c.ig; s.load_pct = c.load;
+        double ms = 0;
+        itpp_status e = time_shape(h, probe_layers, &ms);
+        if (e) return e;
+        ++tried;
+        if (ms < best_ms) { best_ms = ms; best = c; }
+        return ITPP_OK;
+    };
+    // one parameter at a time, each from the best shape so far
+    const int blocks[3] = {128, 256, 512}, grids[3] = {2, 4, 8}, igrids[3] = {4, 8, 16};
+    const int loads[4] = {25, 35, 50, 65};
+    for (int v : blocks) if (v != best.mb) { Shape c = best; c.mb = v; if ((st = try_shape(c))) return h->sticky = st; }
+    for (int v : grids) if (v != best.mg) { Shape c = best; c.mg = v; if ((st = try_shape(c))) return h->sticky = st; }
+    for (int v : igrids) if (v != best.ig) { Shape c = best; c.ig = v; if ((st = try_shape(c))) return h->sticky = st; }
+    for (int v : loads)
+        if (v != best.load && v >= h->load_floor) { Shape c = best; c.load = v; if ((st = try_shape(c))) return h->sticky = st; }
+    s.main_block = best.mb; s.main_grid = best.mg; s.insert_grid = best.ig; s.load_pct = best.load;
+    if (h->layer) {
+        cudaGraphExecDestroy(h->layer);
+        h->layer = nullptr;
+    }
+    // the chosen shape's layer graph, ready for the next apply
+    if (reset_all(h) != ITPP_OK || capture_layer(h) != ITPP_OK ||
+        cudaStreamSynchronize(h->stream) != cudaSuccess)
+        return h->sticky = ITPP_ERR_CUDA;
+    if (out) {
+        std::memset(out, 0, sizeof(*out));
+        out->main_block = best.mb;
+        out->main_grid = best.mg;
+        out->insert_grid = best.ig;
+        out->table_load_pct = best.load;
+        out->ms_per_probe = best_ms;
+        out->ms_per_probe_default = default_ms;
+        out->candidates = tried;
     }
     return ITPP_OK;
 }

@@ -123,6 +123,9 @@ struct BatchState {
     int cap_policy = 0;
     double delta = 0;
     int num_sms = 1, load_pct = 50, probe_limit = 4096;
+    // launch shape (autotuned): branch-emit block (x2 items per thread), grid
+    // multipliers (CTAs per SM) of the branch-emit and table-build kernels
+    int main_block = 256, main_grid = 4, insert_grid = 8;
 };
 
 // Gate `step` of the layer for every instance that has one.

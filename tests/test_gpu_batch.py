@@ -106,3 +106,26 @@ def test_field_sweep_recipe_sampled_instances():
         o = oracle.Oracle(H.n, H.gate_x, H.gate_z, H.alpha, dtau, delta, M, 1)
         o.apply_layers(1)
         assert_same_state(bp.terms(b), o.terms(), f"sweep instance {b} (n={H.n})")
+
+
+def test_autotune_keeps_results_bit_identical():
+    # the tuner resets every instance and installs the fastest shape; any
+    # shape gives the plain run's states
+    hams = [wl.tfim_1d(10, 1.0, 0.7), wl.tfim_1d(14, 1.0, 1.3, periodic=True),
+            wl.tfim_1d(6, 0.8, 2.0), wl.tfim_2d(3, 1.0, 1.5)]
+    dtau, delta = 0.05, 1e-6
+    bp = itpp.BatchPropagator(hams, dtau, delta, 1 << 16, 1)
+    bp.apply_trotter_layer(2)             # state before tuning is discarded
+    r = bp.autotune(probe_layers=2)
+    assert r["main_block"] in (128, 256, 512) and r["main_grid"] in (2, 4, 8)
+    assert r["insert_grid"] in (4, 8, 16) and 25 <= r["table_load_pct"] <= 65
+    assert r["candidates"] >= 8 and r["ms_per_probe"] <= r["ms_per_probe_default"]
+    counts, _ = bp.counts()
+    assert all(int(c) == 1 for c in counts)           # back at the identity
+    assert all(bp.stats(b)["gates_applied"] == 0 for b in range(len(hams)))
+    ors = _oracles(hams, dtau, delta, 1 << 16, 1)
+    for layer in range(3):
+        bp.apply_trotter_layer(1)
+        for o in ors:
+            o.apply_layers(1)
+    _check_all(bp, ors, hams, "after autotune")

@@ -231,6 +231,32 @@ def _lowest_set_bit(a: np.ndarray) -> np.ndarray:
     return out
 
 
+def _first_occurrences(rows: np.ndarray) -> np.ndarray:
+    """Sorted indices of the first occurrence of every distinct row: rows are
+    grouped by a 64-bit mix of their words, and only rows whose mix repeats
+    are compared in full (same result as ``np.unique(axis=0)``'s first
+    indices, without sorting whole rows)."""
+    h = np.zeros(rows.shape[0], dtype=np.uint64)
+    with np.errstate(over="ignore"):
+        for j in range(rows.shape[1]):
+            h ^= rows[:, j] * np.uint64(0x9E3779B97F4A7C15 + 2 * j)
+            h ^= h >> np.uint64(29)
+            h *= np.uint64(0xBF58476D1CE4E5B9)
+    order = np.argsort(h, kind="stable")
+    hs = h[order]
+    rep = np.zeros(rows.shape[0], dtype=bool)
+    eq = hs[1:] == hs[:-1]
+    rep[1:] |= eq
+    rep[:-1] |= eq
+    keep = np.ones(rows.shape[0], dtype=bool)
+    if rep.any():
+        sub = np.sort(order[rep])                      # rows whose mix repeats
+        _, first = np.unique(rows[sub], axis=0, return_index=True)
+        keep[sub] = False
+        keep[sub[first]] = True
+    return np.flatnonzero(keep)
+
+
 def synthetic_state(n: int, M: int, seed: int, delta: float = 1e-6):
     """``M`` distinct random non-identity strings in the TFIM sector, plus
     the identity.
@@ -259,8 +285,7 @@ def synthetic_state(n: int, M: int, seed: int, delta: float = 1e-6):
         x[odd] ^= _lowest_set_bit(z[odd])
         cand = np.concatenate([keys, np.concatenate([x, z], axis=1)])
         cand = cand[cand.any(axis=1)]                 # drop the identity
-        _, first = np.unique(cand, axis=0, return_index=True)
-        keys = cand[np.sort(first)]
+        keys = cand[_first_occurrences(cand)]
     keys = keys[:M]
     keys = keys[rng.permutation(M)]
     X = np.zeros((M + 1, W), dtype=np.uint64)
