@@ -54,6 +54,7 @@ def lib():
         L.oracle_count.argtypes = [ctypes.c_void_p]
         L.oracle_get_terms.argtypes = [ctypes.c_void_p, _u64p, _u64p, _f64p]
         L.oracle_set_terms.argtypes = [ctypes.c_void_p, ctypes.c_uint64, _u64p, _u64p, _f64p]
+        L.oracle_set_max_weight.argtypes = [ctypes.c_void_p, ctypes.c_int]
         L.oracle_coeffs.argtypes = [ctypes.c_void_p, _u64p, _u64p, ctypes.c_int, _f64p]
         L.oracle_expect.restype = ctypes.c_double
         L.oracle_expect.argtypes = [ctypes.c_void_p, _u64p, _u64p, _f64p, ctypes.c_int]
@@ -86,7 +87,8 @@ class OracleError(RuntimeError):
 class Oracle:
     """One propagation: state starts at the identity (Algorithm 1)."""
 
-    def __init__(self, n, gate_x, gate_z, alpha, dtau, delta, cap_M=0, cap_policy=0):
+    def __init__(self, n, gate_x, gate_z, alpha, dtau, delta, cap_M=0, cap_policy=0,
+                 max_weight=0):
         self.n = int(n)
         self.W = (self.n + 63) // 64
         gx, pgx = _u64(gate_x)
@@ -97,6 +99,8 @@ class Oracle:
                                       int(cap_policy))
         if not self._h:
             raise OracleError("oracle_create rejected its arguments")
+        if max_weight:
+            self._check(lib().oracle_set_max_weight(self._h, int(max_weight)))
 
     @classmethod
     def from_workload(cls, wl):

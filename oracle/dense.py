@@ -79,6 +79,29 @@ def trotter_rho(H, dtau, n_layers, rho0=None, gates=None):
     return rho
 
 
+def trotter_rho_weight_cut(H, dtau, n_layers, k):
+    """The Trotter evolution with the Pauli weight cutoff of Sec. II.B after
+    every gate, done on dense matrices: after each ``rho <- V^dagger rho V``
+    the operator is projected onto the strings of weight <= k,
+    ``rho <- sum_{w(P) <= k} Tr(P rho) / 2^n P``, then scaled to unit trace
+    coefficient.  Brute force for small n (4^n projections per gate)."""
+    D = 2 ** H.n
+    xs, zs = all_strings(H.n)
+    basis = [pauli_dense(xs[i], zs[i], H.n) for i in range(xs.shape[0])
+             if sum(bin(int(a) | int(b)).count("1") for a, b in zip(xs[i], zs[i])) <= k]
+    Vs = [sla.expm(-0.5 * H.alpha[j] * dtau * pauli_dense(H.gate_x[j], H.gate_z[j], H.n))
+          for j in range(H.n_gates)]
+    rho = np.eye(D, dtype=complex)
+    for _ in range(n_layers):
+        for V in Vs:
+            rho = V.conj().T @ rho @ V
+            proj = np.zeros_like(rho)
+            for P in basis:
+                proj += (np.trace(P @ rho) / D) * P
+            rho = proj / (np.trace(proj) / D)
+    return rho
+
+
 def pauli_coefficients(rho, n):
     """{(x, z): c_P} for every string, c_P = Tr(P rho) / Tr(rho)."""
     tr = np.trace(rho)

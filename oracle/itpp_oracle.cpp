@@ -20,7 +20,8 @@
 //                                sigma(x,z) = i^{x z} X^x Z^z.
 //   apply_gate .................. Algorithm 1 inner loop: propagate every term
 //                                with Eq. (ITPP_PropRules), accumulate,
-//                                truncate |c| > delta (Sec. II.B), cap (the
+//                                truncate |c| > delta and, when set, the
+//                                Pauli weight cutoff (Sec. II.B), cap (the
 //                                term bound of the "Practical considerations"
 //                                paragraph, Sec. II.C), normalise by the
 //                                identity coefficient: identify it and
@@ -61,6 +62,13 @@ int popcount64(uint64_t v) {
     int c = 0;
     while (v) { v &= v - 1; ++c; }
     return c;
+}
+
+// Pauli weight: the number of non-identity letters, popc(x | z).
+int weight(int W, const Key& k) {
+    int w = 0;
+    for (int i = 0; i < W; ++i) w += popcount64(k.w[i] | k.w[MAXW + i]);
+    return w;
 }
 
 Key make_key(int W, const uint64_t* x, const uint64_t* z) {
@@ -106,6 +114,7 @@ struct Oracle {
     double dtau = 0, delta = 0;
     uint64_t cap_M = 0;
     int cap_policy = 0;
+    int max_weight = 0;        // Pauli weight cutoff (Sec. II.B); 0: none
     std::map<Key, double> rho;
     // per applied gate: the support kept and the normaliser (for the frozen
     // forward used by the adjoint check)
@@ -133,9 +142,12 @@ int apply_gate(Oracle& o, int k) {
             next[R] += (c * msh) * s;                //   - sinh(theta) Q P
         }
     }
-    // threshold truncation: keep |c| > delta, on the accumulated coefficients
+    // threshold truncation: keep |c| > delta, on the accumulated coefficients;
+    // with a weight cutoff k, also drop strings with more than k non-identity
+    // letters (Sec. II.B "Pauli weight cutoff"; the identity has weight 0)
     for (auto it = next.begin(); it != next.end();) {
-        if (std::fabs(it->second) > o.delta) ++it;
+        const bool heavy = o.max_weight > 0 && weight(o.W, it->first) > o.max_weight;
+        if (std::fabs(it->second) > o.delta && !heavy) ++it;
         else {
             if (it->first.is_identity()) return ERR_TRACE_ZERO;
             it = next.erase(it);
@@ -309,6 +321,13 @@ void oracle_get_terms(void* h, uint64_t* x, uint64_t* z, double* c) {
 }
 
 // Replace the state (used for one-gate checks on synthetic states).
+// Pauli weight cutoff k for every later gate (0: none).
+int oracle_set_max_weight(void* h, int k) {
+    if (k < 0) return ERR_ARG;
+    static_cast<Oracle*>(h)->max_weight = k;
+    return OK;
+}
+
 int oracle_set_terms(void* h, uint64_t count, const uint64_t* x, const uint64_t* z,
                      const double* c) {
     Oracle& o = *static_cast<Oracle*>(h);

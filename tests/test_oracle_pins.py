@@ -117,6 +117,39 @@ def test_delta0_random_hamiltonian_n4_vs_dense():
     _compare_dense(H, 0.13, 2)
 
 
+# ---------------------------------------------------------------------------
+# Pauli weight cutoff (Sec. II.B): after every gate only strings with at most
+# k non-identity letters survive.  Dense reference: project onto that span
+# after every gate.
+# ---------------------------------------------------------------------------
+@pytest.mark.parametrize("k", [1, 2, 3])
+def test_weight_cutoff_vs_dense_projection(k):
+    H = wl.random_pauli_hamiltonian(4, 8, 5, max_weight=3)
+    dtau, L = 0.17, 2
+    o = oracle.Oracle(H.n, H.gate_x, H.gate_z, H.alpha, dtau, 0.0, max_weight=k)
+    o.apply_layers(L)
+    got = _coeff_dict(o)
+    ref = dense.pauli_coefficients(dense.trotter_rho_weight_cut(H, dtau, L, k), H.n)
+    scale = max(abs(v) for v in ref.values())
+    for key, v in ref.items():
+        assert abs(v.imag) < 1e-12 * scale
+        assert abs(got.get(key, 0.0) - v.real) <= 1e-12 * scale, (key, got.get(key), v)
+    assert all(bin(x | z).count("1") <= k for x, z in got)
+
+
+def test_weight_cutoff_at_n_changes_nothing():
+    H = wl.tfim_1d(6, 1.0, 0.8, periodic=True)
+    a = oracle.Oracle(H.n, H.gate_x, H.gate_z, H.alpha, 0.1, 1e-9)
+    b = oracle.Oracle(H.n, H.gate_x, H.gate_z, H.alpha, 0.1, 1e-9, max_weight=6)
+    a.apply_layers(4)
+    b.apply_layers(4)
+    assert _coeff_dict(a) == _coeff_dict(b)
+    c = oracle.Oracle(H.n, H.gate_x, H.gate_z, H.alpha, 0.1, 1e-9, max_weight=2)
+    c.apply_layers(4)
+    assert c.count() < a.count()
+    assert all(bin(x | z).count("1") <= 2 for x, z in _coeff_dict(c))
+
+
 @pytest.mark.parametrize("periodic", [False, True])
 def test_delta0_tfim_vs_dense(periodic):
     H = wl.tfim_1d(4, 1.0, 0.7, periodic=periodic)
