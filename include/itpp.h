@@ -87,12 +87,18 @@ typedef struct {
     int merge_path;
     /* Tuning (0 = library default or the autotuned value):
      * table_load_pct: highest load of the merge table, in percent (10..75).
-     * block_threads: threads per CTA of the gate kernels (64..1024, /32).
-     * items_per_thread: terms per thread per tile (1..8). */
+     * block_threads: threads per CTA of the gate kernels (128, 256, 512).
+     * items_per_thread: terms per thread per tile (1, 2, 4; the partitioned
+     * merge holds at most two). */
     int table_load_pct;
     int block_threads;
     int items_per_thread;
-    int reserved[5];
+    /* Pauli weight cutoff (Sec. II.B, "Pauli weight cutoff"): after every
+     * gate, also drop the strings with more than max_weight non-identity
+     * letters (popc(x | z) > max_weight), together with the |c| > delta
+     * test; the identity (weight 0) always stays.  0: no cutoff; 0..128. */
+    int max_weight;
+    int reserved[4];
 } itpp_params;
 
 /* Counters kept on the device and read by itpp_get_stats (synchronising). */

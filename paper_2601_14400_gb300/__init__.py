@@ -33,7 +33,8 @@ class itpp_params(ctypes.Structure):
     _fields_ = [("delta", ctypes.c_double), ("cap_M", ctypes.c_uint64),
                 ("cap_policy", ctypes.c_int), ("merge_path", ctypes.c_int),
                 ("table_load_pct", ctypes.c_int), ("block_threads", ctypes.c_int),
-                ("items_per_thread", ctypes.c_int), ("reserved", ctypes.c_int * 5)]
+                ("items_per_thread", ctypes.c_int), ("max_weight", ctypes.c_int),
+                ("reserved", ctypes.c_int * 4)]
 
 
 class itpp_stats(ctypes.Structure):
@@ -172,7 +173,7 @@ class Propagator:
 
     def __init__(self, n, gate_x, gate_z, alpha, dtau, delta, cap_M, cap_policy=0,
                  merge_path=0, stream=None, table_load_pct=0, block_threads=0,
-                 items_per_thread=0):
+                 items_per_thread=0, max_weight=0):
         self.n = int(n)
         self.W = (self.n + 63) // 64
         gx, pgx = _u64(gate_x)
@@ -187,6 +188,7 @@ class Propagator:
         p.table_load_pct = int(table_load_pct)
         p.block_threads = int(block_threads)
         p.items_per_thread = int(items_per_thread)
+        p.max_weight = int(max_weight)
         h = _vp()
         st = lib().itpp_create(self.n, pgx, pgz, pal, self.n_gates, float(dtau),
                                ctypes.byref(p), _stream_ptr(stream), ctypes.byref(h))
@@ -317,7 +319,8 @@ class Propagator:
 class BatchPropagator:
     """B independent ITPP propagations advanced in shared launches."""
 
-    def __init__(self, hams, dtau, delta, cap_M, cap_policy=0, stream=None, table_load_pct=0):
+    def __init__(self, hams, dtau, delta, cap_M, cap_policy=0, stream=None, table_load_pct=0,
+                 max_weight=0):
         self.B = len(hams)
         self.ns = [int(H.n) for H in hams]
         self.W = (max(self.ns) + 63) // 64
@@ -335,6 +338,7 @@ class BatchPropagator:
         p.cap_M = int(cap_M)
         p.cap_policy = int(cap_policy)
         p.table_load_pct = int(table_load_pct)
+        p.max_weight = int(max_weight)
         h = _vp()
         st = lib().itpp_batch_create(self.B, n.ctypes.data_as(_i32p), ng.ctypes.data_as(_i32p),
                                      pgx, pgz, pal, float(dtau), ctypes.byref(p),

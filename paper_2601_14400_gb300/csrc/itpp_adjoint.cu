@@ -45,6 +45,7 @@ GateArg<W> gate_arg_of(const HostGate& h) {
     g.ch = h.ch;
     g.msh = h.msh;
     g.qyy = h.qyy;
+    g.maxw = h.maxw;
     return g;
 }
 

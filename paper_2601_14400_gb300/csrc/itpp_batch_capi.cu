@@ -89,7 +89,8 @@ DeviceState view(const itpp_batch_ctx* h, int b) {
 }
 
 template <int W>
-void fill_gate(void* dst, const uint64_t* qx, const uint64_t* qz, double alpha, double dtau) {
+void fill_gate(void* dst, const uint64_t* qx, const uint64_t* qz, double alpha, double dtau,
+               int max_weight) {
     GateArg<W> g;
     std::memset(&g, 0, sizeof(g));
     int yy = 0;
@@ -103,6 +104,7 @@ void fill_gate(void* dst, const uint64_t* qx, const uint64_t* qz, double alpha, 
     g.ch = std::cosh(theta);
     g.msh = -std::sinh(theta);
     g.qyy = yy & 3;
+    g.maxw = max_weight ? max_weight : (1 << 30);
     std::memcpy(dst, &g, sizeof(g));
 }
 
@@ -182,6 +184,7 @@ itpp_status itpp_batch_create(int B, const int* n, const int* n_gates, const uin
     if (p->cap_M < 1 || p->cap_M > (1ULL << 31)) return ITPP_ERR_ARG;
     if (p->cap_policy != 0 && p->cap_policy != 1) return ITPP_ERR_ARG;
     if (p->merge_path != 0) return ITPP_ERR_ARG;
+    if (p->max_weight < 0 || p->max_weight > 128) return ITPP_ERR_ARG;
     int max_n = 0, max_g = 0;
     long long total_g = 0;
     for (int b = 0; b < B; ++b) {
@@ -240,8 +243,8 @@ itpp_status itpp_batch_create(int B, const int* n, const int* n_gates, const uin
         for (int b = 0; b < B; ++b)
             for (int j = 0; j < n_gates[b]; ++j, ++k) {
                 void* dst = gates.data() + ((size_t)b * max_g + j) * gsz;
-                if (W == 1) fill_gate<1>(dst, gate_x + k * W, gate_z + k * W, alpha[k], dtau);
-                else fill_gate<2>(dst, gate_x + k * W, gate_z + k * W, alpha[k], dtau);
+                if (W == 1) fill_gate<1>(dst, gate_x + k * W, gate_z + k * W, alpha[k], dtau, p->max_weight);
+                else fill_gate<2>(dst, gate_x + k * W, gate_z + k * W, alpha[k], dtau, p->max_weight);
             }
     }
     const size_t slot = W == 1 ? 32 : 64;

@@ -236,6 +236,7 @@ itpp_status itpp_create(int n, const uint64_t* gate_x, const uint64_t* gate_z,
     if (p->cap_M < 1 || p->cap_M > (1ULL << 31)) return ITPP_ERR_ARG;
     if (p->cap_policy != 0 && p->cap_policy != 1) return ITPP_ERR_ARG;
     if (p->merge_path < 0 || p->merge_path > 2) return ITPP_ERR_ARG;
+    if (p->max_weight < 0 || p->max_weight > 128) return ITPP_ERR_ARG;
     if (p->table_load_pct != 0 && (p->table_load_pct < 10 || p->table_load_pct > 75))
         return ITPP_ERR_ARG;
     if (p->block_threads != 0 && p->block_threads != 128 && p->block_threads != 256 &&
@@ -297,6 +298,7 @@ itpp_status itpp_create(int n, const uint64_t* gate_x, const uint64_t* gate_z,
         g.sh = std::sinh(theta);
         g.chd = std::cosh(theta);
         g.qyy = yy & 3;
+        g.maxw = p->max_weight ? p->max_weight : (1 << 30);
     }
 
     bool ok = true;

@@ -51,6 +51,7 @@ struct GateArg {
     double ch;    // cosh(theta), theta = alpha * dtau
     double msh;   // -sinh(theta)
     int qyy;      // popcount(qx & qz) mod 4 (number of Y letters in Q)
+    int maxw = 1 << 30;   // Pauli weight cutoff (Sec. II.B): keep weight <= maxw
 };
 
 constexpr int kSelBits = 13;                 // radix digit of the top-M select
@@ -186,6 +187,17 @@ __device__ __forceinline__ bool key_is_zero(const PKey<W>& k) {
 #pragma unroll
     for (int w = 0; w < W; ++w) a |= k.x[w] | k.z[w];
     return a == 0;
+}
+
+// Within the Pauli weight cutoff: at most maxw non-identity letters,
+// popc(x | z) <= maxw (a bound of 64W or more never drops a string).
+template <int W>
+__device__ __forceinline__ bool light(const PKey<W>& k, int maxw) {
+    if (maxw >= 64 * W) return true;
+    int w = 0;
+#pragma unroll
+    for (int i = 0; i < W; ++i) w += __popcll(k.x[i] | k.z[i]);
+    return w <= maxw;
 }
 
 // Whether k * Q (Q the gate's string) is the identity, i.e. k == Q.

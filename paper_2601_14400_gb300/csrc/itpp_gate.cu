@@ -25,6 +25,7 @@ static GateArg<W> gate_arg(const HostGate& h) {
     g.ch = h.ch;
     g.msh = h.msh;
     g.qyy = h.qyy;
+    g.maxw = h.maxw;
     return g;
 }
 

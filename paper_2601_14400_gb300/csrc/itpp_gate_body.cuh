@@ -196,8 +196,9 @@ __device__ __forceinline__ void gate_tile(uint64_t t, uint64_t n,
         const double sum = __dadd_rn(a1, __dmul_rn(cpn, m));   // partner QP present
         va[j] = !comm ? c : (found ? sum : a1);         // {P,Q} = 0: unchanged
         vb[j] = b1;
-        bool keep_b = comm && !found && above(b1, dbits);
-        bool keep_a = above(va[j], dbits);
+        // threshold and weight cutoff on the merged children (Sec. II.B)
+        bool keep_b = comm && !found && above(b1, dbits) && light(key_xor(K[j], g), g.maxw);
+        bool keep_a = above(va[j], dbits) && light(K[j], g.maxw);
         if (i < n) {
             if (id) {
                 // the identity: its merged coefficient is the new trace

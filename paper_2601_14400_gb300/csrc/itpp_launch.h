@@ -48,6 +48,7 @@ struct HostGate {
     double ch = 1, msh = 0;  // cosh(theta), -sinh(theta)
     double sh = 0, chd = 1;  // d ch / d theta = sinh(theta), -d msh / d theta = cosh(theta)
     int qyy = 0;
+    int maxw = 1 << 30;      // Pauli weight cutoff (off by default)
     // the window of consecutive gates this gate belongs to (partitioned merge)
     uint64_t keep_x[2] = {~0ULL, ~0ULL}, keep_z[2] = {~0ULL, ~0ULL};   // key bits hashed
     int pair_mode = 1;       // 1: the gate alone, partitioned by its pair key

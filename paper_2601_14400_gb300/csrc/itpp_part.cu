@@ -313,8 +313,9 @@ __device__ __forceinline__ uint32_t part_flags(const PartItem<W>& it, const Gate
     bool eb;
     part_children(it, g, t_keys, t_b, t_tag, va, &eb);
     if (!it.live) return 0u;
-    bool keep_a = above(*va, dbits);
-    const bool keep_b = eb && above(it.b, dbits);
+    // threshold and weight cutoff on the merged children (Sec. II.B)
+    bool keep_a = above(*va, dbits) && light(it.K, g.maxw);
+    const bool keep_b = eb && above(it.b, dbits) && light(key_xor(it.K, g), g.maxw);
     if (key_is_zero(it.K)) {
         ctl->norm[nxt] = *va;
         if (!keep_a) set_status(ctl, ST_TRACE_ZERO, 1);
@@ -568,6 +569,7 @@ static GateArg<W> gate_of(const HostGate& h) {
     g.ch = h.ch;
     g.msh = h.msh;
     g.qyy = h.qyy;
+    g.maxw = h.maxw;
     return g;
 }
 

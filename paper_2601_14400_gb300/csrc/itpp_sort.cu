@@ -128,7 +128,7 @@ k_sort_expand(Bufs<W> B, DevCtl* ctl, GateArg<W> g, SortBufs<W> sb, double delta
         const double a1 = __dmul_rn(c, g.ch);     // cosh(theta) K
         const double b1 = __dmul_rn(c, m);        // -sinh(theta) s QK
         // the identity commutes with every gate, so a pass-through is never it
-        const bool pass = live && !comm && above(c, dbits);
+        const bool pass = live && !comm && above(c, dbits) && light(K, g.maxw);
         const bool kids = live && comm;
         uint32_t tot_p, tot_k;
         const uint32_t off_p = block_exclusive_scan<kSB>(pass ? 1u : 0u, &tot_p, s_scan);
@@ -285,7 +285,8 @@ k_rs_scatter(DevCtl* ctl, SortBufs<W> sb, int src, PassArg pa) {
 // 3. Segmented reduce of the sorted children, truncation, output.
 template <int W>
 __global__ void __launch_bounds__(kSB)
-k_sort_reduce(Bufs<W> B, DevCtl* ctl, SortBufs<W> sb, int src, double delta, uint64_t cap_out) {
+k_sort_reduce(Bufs<W> B, DevCtl* ctl, SortBufs<W> sb, int src, GateArg<W> g, double delta,
+              uint64_t cap_out) {
     __shared__ uint32_t s_scan[kSB / 32];
     __shared__ unsigned long long s_base;
     if (ctl->status) return;
@@ -309,7 +310,7 @@ k_sort_reduce(Bufs<W> B, DevCtl* ctl, SortBufs<W> sb, int src, double delta, uin
                     v = __dadd_rn(v, c[i + 1]);        // the two addends of K
                     if (i + 2 < n && key_eq(k[i + 2], K)) set_status(ctl, ST_STATE, 51);
                 }
-                keep = above(v, dbits);
+                keep = above(v, dbits) && light(K, g.maxw);
                 if (key_is_zero(K)) {
                     ctl->norm[cur ^ 1] = v;            // the merged identity: new trace
                     if (!keep) set_status(ctl, ST_TRACE_ZERO, 52);
@@ -366,6 +367,7 @@ static cudaError_t sorted_w(const DeviceState& s, const HostGate& h, void* scrat
     g.ch = h.ch;
     g.msh = h.msh;
     g.qyy = h.qyy;
+    g.maxw = h.maxw;
     const SortBufs<W> sb = sort_layout<W>(scratch, s.buf_cap);
     PassArg pa[kMaxPass];
     const int npass = plan_passes<W>(s.n, pa);
@@ -387,7 +389,7 @@ static cudaError_t sorted_w(const DeviceState& s, const HostGate& h, void* scrat
         k_rs_scatter<W><<<(int)gt, kSB, 0, st>>>(s.ctl, sb, src, pa[q]);
         src ^= 1;
     }
-    k_sort_reduce<W><<<(int)ge, kSB, 0, st>>>(B, s.ctl, sb, src, s.delta, s.buf_cap);
+    k_sort_reduce<W><<<(int)ge, kSB, 0, st>>>(B, s.ctl, sb, src, g, s.delta, s.buf_cap);
     return cudaGetLastError();
 }
 
