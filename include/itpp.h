@@ -98,7 +98,14 @@ typedef struct {
      * letters (popc(x | z) > max_weight), together with the |c| > delta
      * test; the identity (weight 0) always stays.  0: no cutoff; 0..128. */
     int max_weight;
-    int reserved[4];
+    /* Product formula of a Trotter layer (Sec. II.C): 1 (default, or 0) the
+     * first-order product of the gates in order; 2 the symmetric second-order
+     * (Strang) product, gates 1..G-1 with half angles, gate G with the full
+     * angle, then gates G-1..1 with half angles (2G-1 elementary gates per
+     * layer; itpp_apply_gate indexes that schedule, while itpp_set_alpha and
+     * itpp_adjoint keep taking and returning the G coefficients). */
+    int trotter_order;
+    int reserved[3];
 } itpp_params;
 
 /* Counters kept on the device and read by itpp_get_stats (synchronising). */

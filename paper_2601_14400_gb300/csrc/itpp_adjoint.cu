@@ -602,21 +602,29 @@ extern "C" itpp_status itpp_adjoint(itpp_handle h, int n_layers, int ckpt_every,
         return ITPP_ERR_ARG;
     if (h->gates.empty()) return ITPP_ERR_ARG;
     if (h->sticky) return h->sticky;
+    // gradients per elementary gate of the schedule, then folded onto the
+    // Hamiltonian's coefficients (d alpha_gate / d alpha = src_scale)
+    std::vector<double> g_sched(h->gates.size(), 0.0);
     itpp_status st = h->s.W == 1
-        ? adjoint_w<1>(h, n_layers, ckpt_every, obs_x, obs_z, seed, m, grad_alpha, value)
-        : adjoint_w<2>(h, n_layers, ckpt_every, obs_x, obs_z, seed, m, grad_alpha, value);
+        ? adjoint_w<1>(h, n_layers, ckpt_every, obs_x, obs_z, seed, m, g_sched.data(), value)
+        : adjoint_w<2>(h, n_layers, ckpt_every, obs_x, obs_z, seed, m, g_sched.data(), value);
     if (st == ITPP_ERR_CUDA) h->sticky = st;
+    if (st == ITPP_OK) {
+        for (int k = 0; k < h->user_gates; ++k) grad_alpha[k] = 0.0;
+        for (size_t j = 0; j < g_sched.size(); ++j)
+            grad_alpha[h->src_gate[j]] += g_sched[j] * h->src_scale[j];
+    }
     return st;
 }
 
 extern "C" itpp_status itpp_set_alpha(itpp_handle h, const double* alpha) {
     if (!h || !alpha) return ITPP_ERR_ARG;
-    for (size_t k = 0; k < h->gates.size(); ++k)
+    for (int k = 0; k < h->user_gates; ++k)
         if (!std::isfinite(alpha[k])) return ITPP_ERR_ARG;
     cudaStreamSynchronize(h->stream);
     for (size_t k = 0; k < h->gates.size(); ++k) {
         HostGate& g = h->gates[k];
-        const double theta = alpha[k] * h->dtau;
+        const double theta = (alpha[h->src_gate[k]] * h->src_scale[k]) * h->dtau;
         g.ch = std::cosh(theta);
         g.msh = -std::sinh(theta);
         g.sh = std::sinh(theta);

@@ -237,6 +237,7 @@ itpp_status itpp_create(int n, const uint64_t* gate_x, const uint64_t* gate_z,
     if (p->cap_policy != 0 && p->cap_policy != 1) return ITPP_ERR_ARG;
     if (p->merge_path < 0 || p->merge_path > 2) return ITPP_ERR_ARG;
     if (p->max_weight < 0 || p->max_weight > 128) return ITPP_ERR_ARG;
+    if (p->trotter_order < 0 || p->trotter_order > 2) return ITPP_ERR_ARG;
     if (p->table_load_pct != 0 && (p->table_load_pct < 10 || p->table_load_pct > 75))
         return ITPP_ERR_ARG;
     if (p->block_threads != 0 && p->block_threads != 128 && p->block_threads != 256 &&
@@ -282,17 +283,29 @@ itpp_status itpp_create(int n, const uint64_t* gate_x, const uint64_t* gate_z,
     uint64_t need = (p->cap_M * 100 + load_for_size - 1) / load_for_size;
     s.table_slots = next_pow2(need < 256 ? 256 : need);
 
+    // the layer's schedule: the first-order product, or the symmetric
+    // (Strang) product with half angles around the last term
+    h->user_gates = n_gates;
+    if (p->trotter_order == 2 && n_gates > 1) {
+        for (int k = 0; k < n_gates - 1; ++k) { h->src_gate.push_back(k); h->src_scale.push_back(0.5); }
+        h->src_gate.push_back(n_gates - 1);
+        h->src_scale.push_back(1.0);
+        for (int k = n_gates - 2; k >= 0; --k) { h->src_gate.push_back(k); h->src_scale.push_back(0.5); }
+    } else {
+        for (int k = 0; k < n_gates; ++k) { h->src_gate.push_back(k); h->src_scale.push_back(1.0); }
+    }
     // per-gate weights: theta = alpha * dtau, the angle of Eq. (ITPP_PropRules)
-    h->gates.resize((size_t)n_gates);
-    for (int k = 0; k < n_gates; ++k) {
-        HostGate& g = h->gates[(size_t)k];
+    h->gates.resize(h->src_gate.size());
+    for (size_t j = 0; j < h->gates.size(); ++j) {
+        const int k = h->src_gate[j];
+        HostGate& g = h->gates[j];
         int yy = 0;
         for (int w = 0; w < W; ++w) {
             g.qx[w] = gate_x[(size_t)k * W + w];
             g.qz[w] = gate_z[(size_t)k * W + w];
             yy += popc64(g.qx[w] & g.qz[w]);
         }
-        const double theta = alpha[k] * dtau;
+        const double theta = (alpha[k] * h->src_scale[j]) * dtau;
         g.ch = std::cosh(theta);
         g.msh = -std::sinh(theta);
         g.sh = std::sinh(theta);

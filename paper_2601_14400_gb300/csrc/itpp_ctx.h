@@ -29,7 +29,12 @@ using itpp_detail::kCtlHead;
 
 struct itpp_ctx {
     itpp::DeviceState s;
-    std::vector<itpp::HostGate> gates;
+    std::vector<itpp::HostGate> gates;   // the elementary gates of one layer
+    // gate j of the layer is Hamiltonian term src_gate[j] with coefficient
+    // alpha * src_scale[j] (the first-order product: j, 1; Strang: halves)
+    std::vector<int> src_gate;
+    std::vector<double> src_scale;
+    int user_gates = 0;
     double dtau = 0;
     itpp_params p{};
     cudaStream_t stream = nullptr;

@@ -118,6 +118,48 @@ def test_delta0_random_hamiltonian_n4_vs_dense():
 
 
 # ---------------------------------------------------------------------------
+# Symmetric (Strang) schedule (Sec. II.C): the written-out gate list, and its
+# Trotter error against exact thermal values, second order.  (The plain
+# product is second order in the expectation values too, since
+# rho = S S^dagger is itself symmetric; the schedules differ in the error
+# constant: larger here at h = 1.2, smaller at h = 0.5.)
+# ---------------------------------------------------------------------------
+def test_strang_schedule_structure():
+    H = wl.tfim_1d(4, 1.0, 0.6)
+    S = wl.strang_schedule(H)
+    G = H.n_gates
+    assert S.n_gates == 2 * G - 1
+    for j in range(G - 1):
+        assert np.array_equal(S.gate_x[j], H.gate_x[j]) and S.alpha[j] == 0.5 * H.alpha[j]
+        assert np.array_equal(S.gate_z[2 * G - 2 - j], H.gate_z[j])
+        assert S.alpha[2 * G - 2 - j] == 0.5 * H.alpha[j]
+    assert S.alpha[G - 1] == H.alpha[G - 1]
+    # the halves of a layer add up to each term's full coefficient
+    tot = {}
+    for j in range(S.n_gates):
+        key = (int(S.gate_x[j, 0]), int(S.gate_z[j, 0]))
+        tot[key] = tot.get(key, 0.0) + S.alpha[j]
+    for k in range(G):
+        assert tot[(int(H.gate_x[k, 0]), int(H.gate_z[k, 0]))] == H.alpha[k]
+
+
+@pytest.mark.parametrize("h", [0.5, 1.2])
+def test_strang_error_second_order(h):
+    n, beta = 6, 0.8
+    H = wl.tfim_1d(n, 1.0, h)
+    E = wl.energy_observable(H)
+    exact = dense.thermal_expect(H, beta, E)
+    err = []
+    for L in (4, 8, 16):
+        S = wl.strang_schedule(H)
+        o = oracle.Oracle(n, S.gate_x, S.gate_z, S.alpha, beta / L, 0.0)
+        o.apply_layers(L)
+        err.append(abs(o.expect(E) - exact))
+    for a, b in zip(err, err[1:]):
+        assert 3.5 < a / b < 4.5                # halving the step: error / 4
+
+
+# ---------------------------------------------------------------------------
 # Pauli weight cutoff (Sec. II.B): after every gate only strings with at most
 # k non-identity letters survive.  Dense reference: project onto that span
 # after every gate.

@@ -149,6 +149,21 @@ def tfim_2d(L: int, J=1.0, h=1.0) -> Hamiltonian:
     return Hamiltonian(n, gx, gz, alpha, labels, np.asarray(param, dtype=np.int32))
 
 
+def strang_schedule(H: Hamiltonian) -> Hamiltonian:
+    """The symmetric second-order product of a Trotter layer (Sec. II.C,
+    Strang splitting) written out as a gate list: terms 1..G-1 with half
+    coefficients, term G whole, then terms G-1..1 with half coefficients."""
+    G = H.n_gates
+    if G < 2:
+        return H
+    idx = list(range(G - 1)) + [G - 1] + list(range(G - 2, -1, -1))
+    scale = np.array([0.5] * (G - 1) + [1.0] + [0.5] * (G - 1))
+    return Hamiltonian(H.n, H.gate_x[idx].copy(), H.gate_z[idx].copy(),
+                       np.asarray(H.alpha, dtype=np.float64)[idx] * scale,
+                       [H.labels[i] for i in idx] if H.labels else [],
+                       H.param[idx] if H.param is not None else None)
+
+
 def random_pauli_hamiltonian(n: int, n_terms: int, seed: int,
                              max_weight: int | None = None) -> Hamiltonian:
     """Random non-identity Pauli strings, letters uniform in {X, Y, Z} on a
