@@ -55,6 +55,8 @@ def lib():
         L.oracle_get_terms.argtypes = [ctypes.c_void_p, _u64p, _u64p, _f64p]
         L.oracle_set_terms.argtypes = [ctypes.c_void_p, ctypes.c_uint64, _u64p, _u64p, _f64p]
         L.oracle_set_max_weight.argtypes = [ctypes.c_void_p, ctypes.c_int]
+        L.oracle_expect_psd.argtypes = [ctypes.c_void_p, _u64p, _u64p, _f64p, ctypes.c_int,
+                                        _f64p]
         L.oracle_coeffs.argtypes = [ctypes.c_void_p, _u64p, _u64p, ctypes.c_int, _f64p]
         L.oracle_expect.restype = ctypes.c_double
         L.oracle_expect.argtypes = [ctypes.c_void_p, _u64p, _u64p, _f64p, ctypes.c_int]
@@ -160,6 +162,18 @@ class Oracle:
         oz, poz = _u64(obs.z)
         ow, pow_ = _f64(obs.w)
         return float(lib().oracle_expect(self._h, pox, poz, pow_, int(ow.shape[0])))
+
+
+    def expect_psd(self, obs):
+        """(<O>_{2 tau}, Tr[(O rho) rho] / 2^n, Tr[rho^2] / 2^n, imaginary
+        residual) of the squared state, Sec. II.C."""
+        ox, pox = _u64(obs.x)
+        oz, poz = _u64(obs.z)
+        ow, pow_ = _f64(obs.w)
+        out = np.zeros(4)
+        self._check(lib().oracle_expect_psd(self._h, pox, poz, pow_, int(ow.shape[0]),
+                                            out.ctypes.data_as(_f64p)))
+        return float(out[0]), float(out[1]), float(out[2]), float(out[3])
 
 
 class FrozenAdjoint:

@@ -30,6 +30,10 @@
 //   expect ...................... <O> = Tr[O rho] with the identity
 //                                coefficient equal to one (Sec. II.C, the
 //                                expectation from the propagated operator).
+//   expect_psd .................. <O>_{2 tau} of the squared (positive
+//                                semidefinite) state, Sec. II.C: the Pauli
+//                                expansion of O rho first, then its overlap
+//                                with rho, over the purity (l2 norm).
 //   frozen forward / adjoint .... gradients of the propagated expectation with
 //                                the support of every gate held fixed; the
 //                                paper has no such step, it is the linear
@@ -40,6 +44,7 @@
 #include <cmath>
 #include <cstdint>
 #include <cstring>
+#include <complex>
 #include <map>
 #include <vector>
 
@@ -360,6 +365,41 @@ double oracle_expect(void* h, const uint64_t* ox, const uint64_t* oz, const doub
         if (it != o.rho.end()) s += ow[j] * it->second;
     }
     return s;
+}
+
+// <O>_{2 tau} ~= Tr[(O rho) rho] / Tr[rho^2] (Sec. II.C, restoring positive
+// semidefiniteness by squaring the state).  The product O rho is expanded in
+// the Pauli basis (O_j P = i^e S, complex coefficients summed per string),
+// then overlapped with rho: Tr[S R] = 2^n delta_SR, so Tr[(O rho) rho] / 2^n
+// = sum_S [O rho]_S c_S.  The purity Tr[rho^2] / 2^n is the squared l2 norm
+// of the coefficients.  out: [0] the ratio, [1] the numerator / 2^n, [2] the
+// purity / 2^n, [3] the imaginary part of the numerator (zero up to
+// rounding for Hermitian O and rho).
+int oracle_expect_psd(void* h, const uint64_t* ox, const uint64_t* oz, const double* ow, int m,
+                      double* out) {
+    Oracle& o = *static_cast<Oracle*>(h);
+    std::map<Key, std::complex<double>> prod;                 // O rho
+    const std::complex<double> ipow[4] = {{1, 0}, {0, 1}, {-1, 0}, {0, -1}};
+    for (int j = 0; j < m; ++j) {
+        const Key Oj = make_key(o.W, ox + (size_t)j * o.W, oz + (size_t)j * o.W);
+        for (const auto& [P, c] : o.rho) {
+            Key S;
+            const int e = pauli_product(o.W, Oj, P, &S);      // O_j P = i^e S
+            prod[S] += ow[j] * c * ipow[e & 3];
+        }
+    }
+    std::complex<double> num = 0.0;
+    for (const auto& [S, v] : prod) {
+        auto it = o.rho.find(S);
+        if (it != o.rho.end()) num += v * it->second;
+    }
+    double purity = 0.0;
+    for (const auto& kv : o.rho) purity += kv.second * kv.second;
+    out[0] = num.real() / purity;
+    out[1] = num.real();
+    out[2] = purity;
+    out[3] = num.imag();
+    return OK;
 }
 
 // Run n_layers Trotter layers from the identity, recording the kept support

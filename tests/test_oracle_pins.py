@@ -118,6 +118,51 @@ def test_delta0_random_hamiltonian_n4_vs_dense():
 
 
 # ---------------------------------------------------------------------------
+# PSD-restored observable (Sec. II.C): <O>_{2 tau} = Tr[(O rho) rho] / Tr[rho^2]
+# with the product expanded in the Pauli basis.  Pinned by the dense
+# Tr[O rho^2] / Tr[rho^2] of the same (truncated) operator, and, where the
+# Trotter product is exact (h = 0, all terms commute), by the closed form
+# <Z_i Z_{i+1}> = tanh(2 tau J) of the squared state at beta = 2 tau.
+# ---------------------------------------------------------------------------
+def _dense_from_state(o, n):
+    x, z, c = o.terms()
+    rho = np.zeros((2 ** n, 2 ** n), dtype=complex)
+    for i in range(len(c)):
+        rho += c[i] * dense.pauli_dense(x[i], z[i], n)
+    return rho
+
+
+@pytest.mark.parametrize("obs_kind", ["energy", "zz", "x"])
+def test_psd_observable_vs_dense_square(obs_kind):
+    n = 5
+    H = wl.tfim_1d(n, 1.0, 0.9)
+    o = oracle.Oracle(n, H.gate_x, H.gate_z, H.alpha, 0.1, 2e-3)   # truncated: not exactly PSD
+    o.apply_layers(6)
+    O = {"energy": wl.energy_observable(H), "zz": wl.zz_observables(n, [(1, 2)])[0],
+         "x": wl.x_observables(n)[2]}[obs_kind]
+    val, num, pur, imag = o.expect_psd(O)
+    rho = _dense_from_state(o, n)
+    Od = sum(O.w[j] * dense.pauli_dense(O.x[j], O.z[j], n) for j in range(len(O.w)))
+    r2 = rho @ rho
+    ref = np.trace(Od @ r2) / np.trace(r2)
+    assert abs(ref.imag) < 1e-12 and abs(imag) < 1e-12 * max(1.0, abs(num))
+    assert abs(val - ref.real) <= 1e-12 * max(1.0, abs(ref.real))
+    assert abs(pur - np.trace(r2).real / 2 ** n) <= 1e-12 * pur
+
+
+def test_psd_observable_is_the_state_at_twice_the_imaginary_time():
+    n, J, tau, L = 6, 0.8, 0.35, 5
+    H = wl.tfim_1d(n, J, 0.0)                     # h = 0: the product is exact
+    o = oracle.Oracle(n, H.gate_x, H.gate_z, H.alpha, tau / L, 0.0)
+    o.apply_layers(L)
+    for (a, b) in [(0, 1), (2, 3)]:
+        val, _, _, _ = o.expect_psd(wl.zz_observables(n, [(a, b)])[0])
+        assert abs(val - math.tanh(2 * tau * J)) < 1e-13
+        plain = o.expect(wl.zz_observables(n, [(a, b)])[0])
+        assert abs(plain - math.tanh(tau * J)) < 1e-13
+
+
+# ---------------------------------------------------------------------------
 # Symmetric (Strang) schedule (Sec. II.C): the written-out gate list, and its
 # Trotter error against exact thermal values, second order.  (The plain
 # product is second order in the expectation values too, since
