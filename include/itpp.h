@@ -195,6 +195,22 @@ itpp_status itpp_truncate(itpp_handle h, double delta);
 itpp_status itpp_expect(itpp_handle h, const uint64_t* obs_x, const uint64_t* obs_z,
                         const double* obs_w, int m, double* out);
 
+/* Expectation value of the positive-semidefinite restored state (Sec. II.C,
+ * squaring the approximate operator): <O>_{2 tau} ~= Tr[(O rho) rho] /
+ * Tr[rho^2], the estimate at imaginary time 2 tau from the state at tau.
+ * The product O rho is never expanded: only commuting pairs contribute,
+ * Tr[(O rho) rho] / 2^n = sum_j w_j sum_{[P,O_j]=0} s(O_j,P) c_P c_{O_j P},
+ * found by a lookup of O_j.P in a hash table of the state; the purity
+ * Tr[rho^2] / 2^n is the squared l2 norm of the coefficients.
+ *   obs_x/z, obs_w  host, as itpp_expect; 1 <= m <= 65536.
+ *   out             host, three doubles: <O>_{2 tau}, Tr[(O rho) rho] / 2^n,
+ *                   Tr[rho^2] / 2^n.
+ * Cost: one table build plus m commutation tests per term.  Uses the merge
+ * table's memory (cleared first); the state is unchanged.  Synchronising;
+ * sums are compensated (Kahan) and reduced in a fixed order. */
+itpp_status itpp_expect_psd(itpp_handle h, const uint64_t* obs_x, const uint64_t* obs_z,
+                            const double* obs_w, int m, double* out);
+
 /* The coefficient c_{P_j} of each string (0 where the string is absent).
  * Host arrays; out has m entries.  Synchronising. */
 itpp_status itpp_coeffs(itpp_handle h, const uint64_t* obs_x, const uint64_t* obs_z,

@@ -71,6 +71,7 @@ _SIGNATURES = [
     ("itpp_apply_gate", ctypes.c_int, [_vp, ctypes.c_int]),
     ("itpp_truncate", ctypes.c_int, [_vp, ctypes.c_double]),
     ("itpp_expect", ctypes.c_int, [_vp, _u64p, _u64p, _f64p, ctypes.c_int, _f64p]),
+    ("itpp_expect_psd", ctypes.c_int, [_vp, _u64p, _u64p, _f64p, ctypes.c_int, _f64p]),
     ("itpp_coeffs", ctypes.c_int, [_vp, _u64p, _u64p, ctypes.c_int, _f64p]),
     ("itpp_expect_device", ctypes.c_int, [_vp, _vp, _vp, _vp, ctypes.c_int, _vp]),
     ("itpp_synchronize", ctypes.c_int, [_vp]),
@@ -272,6 +273,17 @@ class Propagator:
         _check(lib().itpp_expect(self._h, pox, poz, pow_, int(ow.shape[0]), ctypes.byref(out)),
                "itpp_expect")
         return float(out.value)
+
+    def expect_psd(self, obs):
+        """(<O>_{2 tau}, Tr[(O rho) rho] / 2^n, Tr[rho^2] / 2^n) of the squared
+        state (Sec. II.C); see include/itpp.h."""
+        ox, pox = _u64(obs.x)
+        oz, poz = _u64(obs.z)
+        ow, pow_ = _f64(obs.w)
+        out = np.zeros(3)
+        _check(lib().itpp_expect_psd(self._h, pox, poz, pow_, int(ow.shape[0]),
+                                     out.ctypes.data_as(_f64p)), "itpp_expect_psd")
+        return float(out[0]), float(out[1]), float(out[2])
 
     def coeffs(self, ox, oz):
         ox, pox = _u64(ox)

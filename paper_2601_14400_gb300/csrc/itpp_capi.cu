@@ -60,6 +60,7 @@ void free_all(itpp_ctx* h) {
     if (h->s.ctl) cudaFree(h->s.ctl);
     if (h->obs_mem) cudaFree(h->obs_mem);
     if (h->sort_mem) cudaFree(h->sort_mem);
+    if (h->psd_mem) cudaFree(h->psd_mem);
     if (h->h_ctl) cudaFreeHost(h->h_ctl);
     for (int k = 0; k < kKinds; ++k)
         for (auto& e : h->ev[k]) { cudaEventDestroy(e.a); cudaEventDestroy(e.b); }
@@ -535,6 +536,40 @@ itpp_status itpp_expect(itpp_handle h, const uint64_t* obs_x, const uint64_t* ob
                         const double* obs_w, int m, double* out) {
     if (!h || !obs_w || !out) return ITPP_ERR_ARG;
     return expect_host(h, obs_x, obs_z, obs_w, m, nullptr, out);
+}
+
+itpp_status itpp_expect_psd(itpp_handle h, const uint64_t* obs_x, const uint64_t* obs_z,
+                            const double* obs_w, int m, double* out) {
+    if (!h || !obs_w || !out) return ITPP_ERR_ARG;
+    itpp_status st = check_obs_args(h, obs_x, obs_z, m);
+    if (st) return st;
+    if (h->sticky) return h->sticky;
+    st = ensure_obs(h, m, h->s.W);
+    if (st) return st;
+    const int n_part = h->s.num_sms * 8;
+    if (!h->psd_mem && cudaMalloc(reinterpret_cast<void**>(&h->psd_mem),
+                                  ((size_t)2 * n_part + 4) * sizeof(double)) != cudaSuccess) {
+        cudaGetLastError();
+        return ITPP_ERR_ALLOC;
+    }
+    ObsPtrs o = obs_layout(h, m, h->s.W);
+    const size_t kb = (size_t)m * h->s.W * 8;
+    if (cudaMemcpyAsync(o.ox, obs_x, kb, cudaMemcpyHostToDevice, h->stream) != cudaSuccess ||
+        cudaMemcpyAsync(o.oz, obs_z, kb, cudaMemcpyHostToDevice, h->stream) != cudaSuccess ||
+        cudaMemcpyAsync(o.ow, obs_w, (size_t)m * 8, cudaMemcpyHostToDevice, h->stream) !=
+            cudaSuccess)
+        return cuda_fail(h);
+    if ((itpp_detail_touch(h), launch_materialize(h->s, h->stream)) != cudaSuccess) return cuda_fail(h);
+    double* d_out = h->psd_mem + 2 * (size_t)n_part;
+    EventPair* ev = prof_begin(h, 3);
+    cudaError_t e = launch_expect_psd(h->s, o.ox, o.oz, o.ow, m, h->psd_mem, n_part, d_out,
+                                      h->stream);
+    prof_end(h, ev);
+    if (e != cudaSuccess) return cuda_fail(h);
+    if (cudaMemcpyAsync(out, d_out, 3 * sizeof(double), cudaMemcpyDeviceToHost, h->stream) !=
+        cudaSuccess)
+        return cuda_fail(h);
+    return sync_ctl(h);
 }
 
 itpp_status itpp_coeffs(itpp_handle h, const uint64_t* obs_x, const uint64_t* obs_z, int m,

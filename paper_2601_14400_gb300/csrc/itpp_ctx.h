@@ -44,6 +44,8 @@ struct itpp_ctx {
     // expectation scratch
     void* obs_mem = nullptr;
     size_t obs_bytes = 0;
+    // PSD-restored observable: block partials and the result
+    double* psd_mem = nullptr;
     // sorted merge scratch
     void* sort_mem = nullptr;
     uint64_t sort_bytes = 0;

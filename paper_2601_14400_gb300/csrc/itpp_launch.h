@@ -94,6 +94,11 @@ int sorted_launches(int n, int W);
 cudaError_t launch_expect(const DeviceState& s, const uint64_t* d_ox, const uint64_t* d_oz,
                           const double* d_ow, int m, int tsize, int* d_tab, int* d_first,
                           double* d_vals, double* d_out, cudaStream_t st);
+// <O>_{2 tau} of the squared state (itpp_psd.cu): d_partials holds
+// 2 * n_part doubles, d_out three (ratio, numerator / 2^n, purity / 2^n).
+cudaError_t launch_expect_psd(const DeviceState& s, const uint64_t* d_ox, const uint64_t* d_oz,
+                              const double* d_ow, int m, double* d_partials, int n_part,
+                              double* d_out, cudaStream_t st);
 // Normalised export into the other buffer's memory: x plane, z plane, c.
 cudaError_t launch_export(const DeviceState& s, uint64_t* d_x, uint64_t* d_z, double* d_c,
                           cudaStream_t st);
