@@ -71,7 +71,10 @@ typedef struct {
      *    error ("terminating").
      * 1: keep the cap_M largest |c| (ties: ascending key, words x[0..W-1]
      *    then z[0..W-1] compared as unsigned), the K-truncation of Sec. II.C
-     *    applied only when the bound is exceeded ("adapting"). */
+     *    applied only when the bound is exceeded ("adapting").  With
+     *    delta = 0 this is the paper's K-truncation proper (K = cap_M, the K
+     *    largest coefficients after every step); each step that dropped
+     *    terms counts in itpp_stats.cap_events. */
     int cap_policy;
     /* How the children of equal strings are found and summed; every path
      * gives bit-identical states.
