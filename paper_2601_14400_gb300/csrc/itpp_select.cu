@@ -68,30 +68,32 @@ struct Pick {
 // histogram of kSelBins counts (global 64-bit counts read through L2, or
 // 32-bit shared ones); NT threads, result in *out (shared).
 template <int NT, bool kGlobal>
+__device__ __forceinline__ unsigned long long hist_at(const void* hist, int b) {
+    return kGlobal ? __ldcg(static_cast<const unsigned long long*>(hist) + b)
+                   : (unsigned long long)static_cast<const unsigned int*>(hist)[b];
+}
+
+template <int NT, bool kGlobal>
 __device__ __forceinline__ void pick_digit(const void* hist, unsigned long long k,
                                            unsigned long long* s_part, Pick* out) {
     constexpr int PER = kSelBins / NT;
     const int t = threadIdx.x;
     if (t == 0) *out = Pick{0, 0, 0};
-    unsigned long long hv[PER], sum = 0;
-#pragma unroll
-    for (int j = 0; j < PER; ++j) {
-        const int b = kSelBins - 1 - PER * t - j;
-        hv[j] = kGlobal ? __ldcg(static_cast<const unsigned long long*>(hist) + b)
-                        : (unsigned long long)static_cast<const unsigned int*>(hist)[b];
-        sum += hv[j];
-    }
+    // two passes over this thread's bins (sum, then find) instead of
+    // holding PER counts in registers
+    unsigned long long sum = 0;
+    for (int j = 0; j < PER; ++j) sum += hist_at<NT, kGlobal>(hist, kSelBins - 1 - PER * t - j);
     const unsigned long long incl = scan_nt<NT>(sum, s_part);
     unsigned long long run = incl - sum;
     if (run < k && k <= incl) {
-#pragma unroll
         for (int j = 0; j < PER; ++j) {
-            if (run < k && k <= run + hv[j]) {
+            const unsigned long long hv = hist_at<NT, kGlobal>(hist, kSelBins - 1 - PER * t - j);
+            if (run < k && k <= run + hv) {
                 out->digit = kSelBins - 1 - PER * t - j;
                 out->k_in = k - run;
-                out->count = hv[j];
+                out->count = hv;
             }
-            run += hv[j];
+            run += hv;
         }
     }
     __syncthreads();
@@ -101,7 +103,7 @@ __device__ __forceinline__ void pick_digit(const void* hist, unsigned long long 
 // 1. First digit
 // ---------------------------------------------------------------------------
 template <int W>
-__global__ void __launch_bounds__(256)
+__global__ void __launch_bounds__(256, 4)
 k_sel_hist(Bufs<W> B, DevCtl* ctl, unsigned long long lo) {
     __shared__ unsigned int h[kSelBins];
     __shared__ unsigned long long s_part[256];
@@ -114,21 +116,24 @@ k_sel_hist(Bufs<W> B, DevCtl* ctl, unsigned long long lo) {
     __syncthreads();
     const int cur = ctl->cur;
     const uint64_t n = live_count(ctl, cur);
-    const double* __restrict__ c = B.c[cur];
+    // the coefficients' bit patterns, read as integers (no floating point);
     // eight independent loads in flight per thread, then their counts
+    const unsigned long long* __restrict__ c =
+        reinterpret_cast<const unsigned long long*>(B.c[cur]);
     constexpr int U = 8;
     const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
     for (uint64_t i0 = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i0 < n; i0 += U * stride) {
-        double v[U];
+        unsigned long long v[U];
 #pragma unroll
         for (int u = 0; u < U; ++u) {
             const uint64_t i = i0 + (uint64_t)u * stride;
-            v[u] = i < n ? __ldcs(c + i) : -1.0;
+            v[u] = i < n ? __ldcs(c + i) : 0ULL;
         }
 #pragma unroll
         for (int u = 0; u < U; ++u) {
-            if (v[u] == -1.0 && i0 + (uint64_t)u * stride >= n) continue;
-            unsigned long long d = sel_value(v[u], lo) >> sh;
+            if (i0 + (uint64_t)u * stride >= n) break;
+            const unsigned long long b = v[u] & 0x7fffffffffffffffULL;   // |c| pattern
+            unsigned long long d = (b > lo ? b - lo : 0ULL) >> sh;
             if (d > (unsigned long long)(kSelBins - 1)) d = kSelBins - 1;   // not reached: hi is the max
             atomicAdd(&h[d], 1u);
         }
