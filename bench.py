@@ -68,6 +68,8 @@ def parse():
     ap.add_argument("--block", type=int, default=0, help="threads per CTA of the gate kernels")
     ap.add_argument("--ipt", type=int, default=0, help="terms per thread per tile")
     ap.add_argument("--merge-path", type=int, default=0)
+    ap.add_argument("--partition-target", type=int, default=0,
+                    help="mean partition size of the partitioned merge (0: library default)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--mode", default="headline", choices=["headline", "batch", "adjoint", "synth"],
@@ -450,7 +452,8 @@ def main():
 
     stream = torch.cuda.Stream()
     g = itpp.Propagator.from_workload(w, stream=stream, block_threads=args.block,
-                                      items_per_thread=args.ipt, merge_path=args.merge_path)
+                                      items_per_thread=args.ipt, merge_path=args.merge_path,
+                                      partition_target=args.partition_target)
     W = w.H.W
     term_bytes = 16 * W + 8
 

@@ -108,7 +108,12 @@ typedef struct {
      * layer; itpp_apply_gate indexes that schedule, while itpp_set_alpha and
      * itpp_adjoint keep taking and returning the G coefficients). */
     int trotter_order;
-    int reserved[3];
+    /* Partitioned merge (merge_path 0): the mean partition size the scatter
+     * aims for, 64..2048 terms (0: the library default).  Larger partitions
+     * amortise the per-partition work, smaller ones keep a window's grown
+     * segments inside one CTA's register chunk. */
+    int partition_target;
+    int reserved[2];
 } itpp_params;
 
 /* Counters kept on the device and read by itpp_get_stats (synchronising). */

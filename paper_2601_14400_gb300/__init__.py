@@ -34,7 +34,8 @@ class itpp_params(ctypes.Structure):
                 ("cap_policy", ctypes.c_int), ("merge_path", ctypes.c_int),
                 ("table_load_pct", ctypes.c_int), ("block_threads", ctypes.c_int),
                 ("items_per_thread", ctypes.c_int), ("max_weight", ctypes.c_int),
-                ("trotter_order", ctypes.c_int), ("reserved", ctypes.c_int * 3)]
+                ("trotter_order", ctypes.c_int), ("partition_target", ctypes.c_int),
+                ("reserved", ctypes.c_int * 2)]
 
 
 class itpp_stats(ctypes.Structure):
@@ -174,7 +175,7 @@ class Propagator:
 
     def __init__(self, n, gate_x, gate_z, alpha, dtau, delta, cap_M, cap_policy=0,
                  merge_path=0, stream=None, table_load_pct=0, block_threads=0,
-                 items_per_thread=0, max_weight=0, trotter_order=1):
+                 items_per_thread=0, max_weight=0, trotter_order=1, partition_target=0):
         self.n = int(n)
         self.W = (self.n + 63) // 64
         gx, pgx = _u64(gate_x)
@@ -191,6 +192,7 @@ class Propagator:
         p.items_per_thread = int(items_per_thread)
         p.max_weight = int(max_weight)
         p.trotter_order = int(trotter_order)
+        p.partition_target = int(partition_target)
         h = _vp()
         st = lib().itpp_create(self.n, pgx, pgz, pal, self.n_gates, float(dtau),
                                ctypes.byref(p), _stream_ptr(stream), ctypes.byref(h))

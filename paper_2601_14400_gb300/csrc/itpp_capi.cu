@@ -239,6 +239,8 @@ itpp_status itpp_create(int n, const uint64_t* gate_x, const uint64_t* gate_z,
     if (p->merge_path < 0 || p->merge_path > 2) return ITPP_ERR_ARG;
     if (p->max_weight < 0 || p->max_weight > 128) return ITPP_ERR_ARG;
     if (p->trotter_order < 0 || p->trotter_order > 2) return ITPP_ERR_ARG;
+    if (p->partition_target != 0 && (p->partition_target < 64 || p->partition_target > 2048))
+        return ITPP_ERR_ARG;
     if (p->table_load_pct != 0 && (p->table_load_pct < 10 || p->table_load_pct > 75))
         return ITPP_ERR_ARG;
     if (p->block_threads != 0 && p->block_threads != 128 && p->block_threads != 256 &&
@@ -327,7 +329,8 @@ itpp_status itpp_create(int n, const uint64_t* gate_x, const uint64_t* gate_z,
         // the scatter buffer: partitions of a fixed stride, 2.5x the mean
         // partition at the bound (a window group adds up to 4^sites terms)
         s.part_cap = 2 * p->cap_M + p->cap_M / 2 + (1ULL << 18);
-        s.part_max = partition_max(W, p->cap_M);
+        s.part_target = p->partition_target ? p->partition_target : partition_target_default(W);
+        s.part_max = partition_max(p->cap_M, s.part_target);
         ok &= cudaMalloc(&s.part_keys, s.part_cap * 16 * W) == cudaSuccess;
         ok &= ok && cudaMalloc(reinterpret_cast<void**>(&s.part_coef), s.part_cap * 8) == cudaSuccess;
         ok &= ok && cudaMalloc(reinterpret_cast<void**>(&s.part_cursor),

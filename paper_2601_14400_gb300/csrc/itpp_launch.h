@@ -38,6 +38,7 @@ struct DeviceState {
     PartDesc* part_desc[2] = {nullptr, nullptr};   // [part_max] per state buffer
     uint64_t part_cap = 0;
     uint32_t part_max = 0;
+    int part_target = 0;              // mean partition size of the scatter
     // top-M select leaves its kept set as a predicate for the next scatter
     bool merge_deferred = false;
 };
@@ -68,7 +69,8 @@ cudaError_t launch_gate_post(const DeviceState& s, cudaStream_t st);
 cudaError_t launch_part_scatter(const DeviceState& s, const HostGate& g, int force,
                                 cudaStream_t st);
 cudaError_t launch_part_merge(const DeviceState& s, const HostGate& g, cudaStream_t st);
-uint32_t partition_max(int W, uint64_t cap_M);
+uint32_t partition_max(uint64_t cap_M, int target);
+int partition_target_default(int W);
 // Group consecutive gates into windows of at most a few sites (sets the
 // window fields of every gate).
 void plan_windows(int W, std::vector<HostGate>& gates);

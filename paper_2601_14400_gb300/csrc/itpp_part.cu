@@ -33,7 +33,7 @@ namespace {
 // largest window (sites; a group holds at most 4^sites terms).
 template <int W> struct PartGeom;
 template <> struct PartGeom<1> {
-    static constexpr int kSlots = 2048, kTarget = 600, kSplit = 1400, kWinSites = 5;
+    static constexpr int kSlots = 2048, kTarget = 700, kSplit = 1400, kWinSites = 5;
 };
 template <> struct PartGeom<2> {
     static constexpr int kSlots = 1024, kTarget = 300, kSplit = 700, kWinSites = 4;
@@ -129,7 +129,7 @@ template <int W>
 __global__ void __launch_bounds__(256)
 k_part_scatter(Bufs<W> B, DevCtl* ctl, PKey<W>* pk, double* pc, unsigned int* cursor,
                uint64_t pbuf_cap, uint32_t p_max, GateArg<W> g, PartFn<W> f, int force,
-               int n_sites) {
+               int n_sites, int target) {
     if (ctl->status) return;
     const int cur = ctl->cur;
     if (!force && !ctl->need_scatter) {
@@ -140,7 +140,7 @@ k_part_scatter(Bufs<W> B, DevCtl* ctl, PKey<W>* pk, double* pc, unsigned int* cu
         return;
     }
     const uint64_t n = live_count(ctl, cur);
-    const PartPlan pl = part_plan(n, pbuf_cap, p_max, PartGeom<W>::kTarget);
+    const PartPlan pl = part_plan(n, pbuf_cap, p_max, target);
     const bool fallback = !f.pair && !window_fits(n_sites, f.sites, n);
     if (fallback) f.pair = 1;
     if (blockIdx.x == 0 && threadIdx.x == 0) {
@@ -156,38 +156,50 @@ k_part_scatter(Bufs<W> B, DevCtl* ctl, PKey<W>* pk, double* pc, unsigned int* cu
     const Pending<W> pd = pending_of<W>(ctl);
     uint64_t n_scan = n;
     if (pd.on) n_scan = ctl->pend_n < ctl->buf_cap ? ctl->pend_n : ctl->buf_cap;
-    // whole warps iterate together (the cursor claim below is warp-wide)
+    // whole warps iterate together (the cursor claim below is warp-wide);
+    // U items per thread per round, their loads issued before any claim
+    constexpr int U = 4;
     const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
     const unsigned int lt = (1u << (threadIdx.x & 31)) - 1u;
-    for (uint64_t i0 = (uint64_t)blockIdx.x * blockDim.x; i0 < n_scan; i0 += stride) {
-        const uint64_t i = i0 + threadIdx.x;
-        PKey<W> K;
-        double c = 0.0;
-        bool live = i < n_scan;
-        if (live) {
-            K = load_key_stream(kin + i);
-            c = __ldcs(cin + i);
-            if (pd.on && !cap_keep(K, c, pd.T, pd.all_ties, pd.tk)) {
-                if (key_is_zero(K)) set_status(ctl, ST_TRACE_ZERO, 42);
-                live = false;
+    for (uint64_t i0 = (uint64_t)blockIdx.x * blockDim.x; i0 < n_scan; i0 += U * stride) {
+        PKey<W> K[U];
+        double c[U];
+        bool live[U];
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            const uint64_t i = i0 + (uint64_t)u * stride + threadIdx.x;
+            live[u] = i < n_scan;
+            c[u] = 0.0;
+#pragma unroll
+            for (int w = 0; w < W; ++w) { K[u].x[w] = 0; K[u].z[w] = 0; }
+            if (live[u]) {
+                K[u] = load_key_stream(kin + i);
+                c[u] = __ldcs(cin + i);
             }
         }
-        // one cursor claim per distinct partition in the warp: terms of one
-        // group arrive together and would otherwise serialise on its cursor
-        const uint32_t p = live ? part_of(K, g, f, pl.P) : 0xffffffffu;
-        const unsigned int peers = __match_any_sync(0xffffffffu, p);
-        const int leader = __ffs(peers) - 1;
-        unsigned int base = 0;
-        if (live && (threadIdx.x & 31) == leader) base = atomicAdd(cursor + p, __popc(peers));
-        base = __shfl_sync(0xffffffffu, base, leader);
-        if (live) {
-            const unsigned int pos = base + __popc(peers & lt);
-            if (pos < pl.R) {
-                const uint64_t d = (uint64_t)p * pl.R + pos;
-                pk[d] = K;
-                pc[d] = c;
-            } else {
-                set_status(ctl, ST_CAPACITY, 40);
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            if (live[u] && pd.on && !cap_keep(K[u], c[u], pd.T, pd.all_ties, pd.tk)) {
+                if (key_is_zero(K[u])) set_status(ctl, ST_TRACE_ZERO, 42);
+                live[u] = false;
+            }
+            // one cursor claim per distinct partition in the warp: terms of
+            // one group arrive together and would otherwise serialise on it
+            const uint32_t p = live[u] ? part_of(K[u], g, f, pl.P) : 0xffffffffu;
+            const unsigned int peers = __match_any_sync(0xffffffffu, p);
+            const int leader = __ffs(peers) - 1;
+            unsigned int base = 0;
+            if (live[u] && (threadIdx.x & 31) == leader) base = atomicAdd(cursor + p, __popc(peers));
+            base = __shfl_sync(0xffffffffu, base, leader);
+            if (live[u]) {
+                const unsigned int pos = base + __popc(peers & lt);
+                if (pos < pl.R) {
+                    const uint64_t d = (uint64_t)p * pl.R + pos;
+                    pk[d] = K[u];
+                    pc[d] = c[u];
+                } else {
+                    set_status(ctl, ST_CAPACITY, 40);
+                }
             }
         }
     }
@@ -602,7 +614,7 @@ static cudaError_t scatter_w(const DeviceState& s, const HostGate& h, int force,
                                                reinterpret_cast<PKey<W>*>(s.part_keys),
                                                s.part_coef, s.part_cursor, s.part_cap,
                                                s.part_max, gate_of<W>(h), part_fn_of<W>(h), force,
-                                               s.n);
+                                               s.n, s.part_target);
     return cudaGetLastError();
 }
 
@@ -690,8 +702,12 @@ void plan_windows(int W, std::vector<HostGate>& gates) {
     }
 }
 
-uint32_t partition_max(int W, uint64_t cap_M) {
-    const uint64_t t = W == 1 ? PartGeom<1>::kTarget : PartGeom<2>::kTarget;
+int partition_target_default(int W) {
+    return W == 1 ? PartGeom<1>::kTarget : PartGeom<2>::kTarget;
+}
+
+uint32_t partition_max(uint64_t cap_M, int target) {
+    const uint64_t t = (uint64_t)target;
     return (uint32_t)((cap_M + t - 1) / t + 1);
 }
 
