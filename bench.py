@@ -476,18 +476,20 @@ def main():
     clocks.start()
     barrier(world)
     torch.cuda.synchronize()
-    ev0 = torch.cuda.Event(enable_timing=True)
-    ev1 = torch.cuda.Event(enable_timing=True)
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps + 1)]
+    ev0, ev1 = ev[0], ev[-1]
     torch.cuda.profiler.start()   # ncu --profile-from-start off: timed launches only
     ev0.record(stream)
-    g.apply_trotter_layer(args.steps)
-    ev1.record(stream)
+    for k in range(args.steps):   # one event between layers: per-layer times
+        g.apply_trotter_layer(1)
+        ev[k + 1].record(stream)
     g.synchronize()
     torch.cuda.synchronize()
     torch.cuda.profiler.stop()
     barrier(world)
     clk = clocks.stop()
     ms = ev0.elapsed_time(ev1)
+    layer_ms = [ev[k].elapsed_time(ev[k + 1]) for k in range(args.steps)]
     st1 = g.stats()
     prof = {k: g.profile_read(k) for k in range(4)}
     g.profile_enable(False)
@@ -588,6 +590,17 @@ def main():
             "e2e": e2e,
             "cpu_baseline": cpu,
             "gpu_launches": int(launches),
+            # per-layer device times (an event between layers); the state sits at
+            # its bound M through the timed region, so each layer's N_in is close
+            # to the mean, which the per-layer rates use
+            "layers": {"ms": [round(x, 3) for x in layer_ms],
+                       "median_ms": sorted(layer_ms)[len(layer_ms) // 2],
+                       "best_ms": min(layer_ms),
+                       "mean_terms_in": terms_in / max(args.steps, 1),
+                       "median_terms_per_s": (terms_in / max(args.steps, 1)) /
+                                             (sorted(layer_ms)[len(layer_ms) // 2] * 1e-3),
+                       "best_terms_per_s": (terms_in / max(args.steps, 1)) /
+                                           (min(layer_ms) * 1e-3)},
             "timed_gates": int(gates),
             "table_probes_per_term": (st1["table_probes"] - st0["table_probes"]) / max(terms_in, 1),
             "repartitions_per_gate": (st1["repartitions"] - st0["repartitions"]) / max(gates, 1),
