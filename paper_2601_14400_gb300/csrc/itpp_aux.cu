@@ -11,6 +11,9 @@ template <int W>
 struct BufsA {
     PKey<W>* k[2];
     double* c[2];
+    // by compare-select (a dynamic index copies the array to local memory)
+    __device__ __forceinline__ PKey<W>* key(int i) const { return i ? k[1] : k[0]; }
+    __device__ __forceinline__ double* coef(int i) const { return i ? c[1] : c[0]; }
 };
 
 template <int W>
@@ -82,13 +85,13 @@ k_obs_scan(BufsA<W> B, DevCtl* ctl, const uint64_t* __restrict__ ox,
     const uint64_t mask = (uint64_t)tsize - 1;
     for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
          i += (uint64_t)gridDim.x * blockDim.x) {
-        const PKey<W> K = load_key(B.k[cur] + i);
+        const PKey<W> K = load_key(B.key(cur) + i);
         uint64_t h = key_hash(K) & mask;
         for (int p = 0; p < tsize; ++p) {
             const int e = __ldg(tab + h);
             if (e < 0) break;
             if (key_eq(key_from_planes<W>(ox, oz, (uint64_t)e), K)) {
-                vals[e] = normalised(__ldg(B.c[cur] + i), rnorm, key_is_zero(K));
+                vals[e] = normalised(__ldg(B.coef(cur) + i), rnorm, key_is_zero(K));
                 break;
             }
             h = (h + 1) & mask;
@@ -161,10 +164,10 @@ k_export(BufsA<W> B, const DevCtl* ctl, uint64_t* xo, uint64_t* zo, double* co) 
     const double rnorm = ctl->rnorm[cur];
     for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
          i += (uint64_t)gridDim.x * blockDim.x) {
-        const PKey<W> K = load_key(B.k[cur] + i);
+        const PKey<W> K = load_key(B.key(cur) + i);
 #pragma unroll
         for (int w = 0; w < W; ++w) { xo[i * W + w] = K.x[w]; zo[i * W + w] = K.z[w]; }
-        co[i] = normalised(B.c[cur][i], rnorm, key_is_zero(K));
+        co[i] = normalised(B.coef(cur)[i], rnorm, key_is_zero(K));
     }
 }
 
@@ -229,8 +232,8 @@ k_import(BufsA<W> B, DevCtl* ctl, const uint64_t* x, const uint64_t* z, const do
             if (ci == 0.0) set_status(ctl, ST_TRACE_ZERO, 10);
             atomicAdd(&ctl->sel_k, 1ULL);
         }
-        B.k[0][i] = K;
-        B.c[0][i] = ci;
+        B.key(0)[i] = K;
+        B.coef(0)[i] = ci;
         // table insert for the duplicate check (key -> index)
         uint64_t h = key_hash(K) & mask;
         int p = 0;
@@ -263,7 +266,7 @@ k_import_check(const BufsA<W> B, DevCtl* ctl, uint64_t count, const Slot<W>* tab
     const uint64_t mask = table_mask(count, alloc_slots, 50);
     for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < count;
          i += (uint64_t)gridDim.x * blockDim.x) {
-        const PKey<W> K = B.k[0][i];
+        const PKey<W> K = B.key(0)[i];
         uint64_t h = key_hash(K) & mask;
         for (int p = 0; p < probe_limit; ++p) {
             const Slot<W>* s = table + h;
@@ -315,8 +318,8 @@ __global__ void k_reset_identity(BufsA<W> B, DevCtl* ctl) {
     if (threadIdx.x == 0 && blockIdx.x == 0) {
         PKey<W> I;
         for (int w = 0; w < W; ++w) { I.x[w] = 0; I.z[w] = 0; }
-        B.k[0][0] = I;
-        B.c[0][0] = 1.0;
+        B.key(0)[0] = I;
+        B.coef(0)[0] = 1.0;
         ctl->cur = 0;
         ctl->count[0] = 1;
         ctl->count[1] = 0;
@@ -375,8 +378,8 @@ k_trunc(BufsA<W> B, DevCtl* ctl, double delta) {
         double c = 0;
         bool keep = false;
         if (i < n) {
-            K = load_key_stream(B.k[cur] + i);
-            c = normalised(__ldcs(B.c[cur] + i), rnorm, key_is_zero(K));
+            K = load_key_stream(B.key(cur) + i);
+            c = normalised(__ldcs(B.coef(cur) + i), rnorm, key_is_zero(K));
             keep = above(c, (unsigned long long)__double_as_longlong(delta));
             if (key_is_zero(K) && !keep) {
                 set_status(ctl, ST_TRACE_ZERO, 20);
@@ -389,8 +392,8 @@ k_trunc(BufsA<W> B, DevCtl* ctl, double delta) {
             s_base = tot ? atomicAdd(&ctl->count[cur ^ 1], (unsigned long long)tot) : 0ULL;
         __syncthreads();
         if (keep) {
-            store_key_stream(B.k[cur ^ 1] + s_base + off, K);
-            __stcs(B.c[cur ^ 1] + s_base + off, c);
+            store_key_stream(B.key(cur ^ 1) + s_base + off, K);
+            __stcs(B.coef(cur ^ 1) + s_base + off, c);
         }
     }
 }

@@ -310,6 +310,17 @@ __device__ __forceinline__ PKey<W> load_key(const PKey<W>* p) {
 }
 
 template <int W>
+__device__ __forceinline__ void store_key(PKey<W>* p, const PKey<W>& k) {
+    ulonglong2* v = reinterpret_cast<ulonglong2*>(p);
+    if constexpr (W == 1) {
+        *v = make_ulonglong2(k.x[0], k.z[0]);
+    } else {
+        v[0] = make_ulonglong2(k.x[0], k.x[1]);
+        v[1] = make_ulonglong2(k.z[0], k.z[1]);
+    }
+}
+
+template <int W>
 __device__ __forceinline__ void store_key_stream(PKey<W>* p, const PKey<W>& k) {
     ulonglong2* v = reinterpret_cast<ulonglong2*>(p);
     if constexpr (W == 1) {

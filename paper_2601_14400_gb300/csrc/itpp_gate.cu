@@ -50,7 +50,7 @@ k_gate_insert(Bufs<W> B, DevCtl* ctl, Slot<W>* table, uint64_t alloc_slots, int 
     int probes = 0;
     for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
          i += (uint64_t)gridDim.x * blockDim.x)
-        insert_one(B.k[cur], B.c[cur], i, ctl, table, mask, gen, g, probe_limit, &probes);
+        insert_one(B.key(cur), B.coef(cur), i, ctl, table, mask, gen, g, probe_limit, &probes);
     flush_probes(ctl, probes);
 }
 
@@ -75,7 +75,7 @@ k_gate_main(Bufs<W> B, DevCtl* ctl, const Slot<W>* __restrict__ table, uint64_t 
     int probes = 0;
     const GlobalLookup<W> lk{table, mask, gen, probe_limit, ctl, &probes};
     for (uint64_t t = blockIdx.x; t < tiles; t += gridDim.x)
-        gate_tile<W, BLOCK, IPT>(t, n, B.k[cur], B.c[cur], B.k[cur ^ 1], B.c[cur ^ 1], ctl, cur,
+        gate_tile<W, BLOCK, IPT>(t, n, B.key(cur), B.coef(cur), B.key(cur ^ 1), B.coef(cur ^ 1), ctl, cur,
                                  lk, g, rnorm, dbits, cap_out, s_scan, &s_base);
     flush_probes(ctl, probes);
 }
@@ -105,7 +105,7 @@ k_cap_hist(Bufs<W> B, DevCtl* ctl, int shift) {
     const int cur = ctl->cur;
     const uint64_t n = live_count(ctl, cur);
     const unsigned long long prefix = ctl->sel_prefix, mask = ctl->sel_mask;
-    const double* __restrict__ c = B.c[cur];
+    const double* __restrict__ c = B.coef(cur);
     for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
          i += (uint64_t)gridDim.x * blockDim.x) {
         const unsigned long long b = abs_bits(__ldg(c + i));
@@ -142,13 +142,13 @@ k_cap_ties(Bufs<W> B, DevCtl* ctl, PKey<W>* tie_list) {
     const uint64_t tiles = (n + BLOCK - 1) / BLOCK;
     for (uint64_t t = blockIdx.x; t < tiles; t += gridDim.x) {
         const uint64_t i = t * BLOCK + threadIdx.x;
-        const bool tie = i < n && abs_bits(__ldg(B.c[cur] + i)) == T;
+        const bool tie = i < n && abs_bits(__ldg(B.coef(cur) + i)) == T;
         uint32_t tot;
         const uint32_t off = block_exclusive_scan<BLOCK>(tie ? 1u : 0u, &tot, s_scan);
         if (threadIdx.x == 0)
             s_base = tot ? atomicAdd(&ctl->sel_tie_n, (unsigned long long)tot) : 0ULL;
         __syncthreads();
-        if (tie) tie_list[s_base + off] = load_key(B.k[cur] + i);
+        if (tie) tie_list[s_base + off] = load_key(B.key(cur) + i);
     }
 }
 
@@ -194,8 +194,8 @@ k_cap_compact(Bufs<W> B, DevCtl* ctl) {
         double c = 0;
         bool keep = false;
         if (i < n) {
-            K = load_key_stream(B.k[cur] + i);
-            c = __ldcs(B.c[cur] + i);
+            K = load_key_stream(B.key(cur) + i);
+            c = __ldcs(B.coef(cur) + i);
             keep = cap_keep(K, c, T, all_ties, tk);
             if (key_is_zero(K) && !keep) set_status(ctl, ST_TRACE_ZERO, 2);
         }
@@ -205,8 +205,8 @@ k_cap_compact(Bufs<W> B, DevCtl* ctl) {
             s_base = tot ? atomicAdd(&ctl->count[cur ^ 1], (unsigned long long)tot) : 0ULL;
         __syncthreads();
         if (keep) {
-            store_key_stream(B.k[cur ^ 1] + s_base + off, K);
-            __stcs(B.c[cur ^ 1] + s_base + off, c);
+            store_key_stream(B.key(cur ^ 1) + s_base + off, K);
+            __stcs(B.coef(cur ^ 1) + s_base + off, c);
         }
     }
 }
@@ -255,8 +255,8 @@ k_materialize(Bufs<W> B, DevCtl* ctl) {
         double c = 0;
         bool keep = false;
         if (i < n) {
-            K = load_key_stream(B.k[cur] + i);
-            c = __ldcs(B.c[cur] + i);
+            K = load_key_stream(B.key(cur) + i);
+            c = __ldcs(B.coef(cur) + i);
             keep = cap_keep(K, c, T, all_ties, tk);
             if (key_is_zero(K) && !keep) set_status(ctl, ST_TRACE_ZERO, 3);
         }
@@ -266,8 +266,8 @@ k_materialize(Bufs<W> B, DevCtl* ctl) {
             s_base = tot ? atomicAdd(&ctl->count[cur ^ 1], (unsigned long long)tot) : 0ULL;
         __syncthreads();
         if (keep) {
-            store_key_stream(B.k[cur ^ 1] + s_base + off, K);
-            __stcs(B.c[cur ^ 1] + s_base + off, c);
+            store_key_stream(B.key(cur ^ 1) + s_base + off, K);
+            __stcs(B.coef(cur ^ 1) + s_base + off, c);
         }
     }
 }

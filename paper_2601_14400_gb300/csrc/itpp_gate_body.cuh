@@ -25,6 +25,10 @@ template <int W>
 struct Bufs {
     PKey<W>* k[2];
     double* c[2];
+    // by compare-select: a dynamic index into a kernel parameter array
+    // makes the compiler copy the array to local memory
+    __device__ __forceinline__ PKey<W>* key(int i) const { return i ? k[1] : k[0]; }
+    __device__ __forceinline__ double* coef(int i) const { return i ? c[1] : c[0]; }
 };
 
 // ---------------------------------------------------------------------------

@@ -67,8 +67,7 @@ struct PartFn {
     uint64_t kx[W], kz[W];   // bits kept by the mask
     int pair;                // 1: pair-key mode
     int sites;               // sites of the window (mask mode)
-    int word;                // pivot: 0..W-1 x[word], W..2W-1 z[word-W]; -1: Q = I
-    uint64_t bit;
+    uint64_t px[W], pz[W];   // the pivot: the gate's lowest bit (all zero for Q = I)
 };
 
 // Mask mode needs many more possible groups than terms: a group (the terms
@@ -86,16 +85,20 @@ __device__ __forceinline__ bool window_fits(int n_sites, int w_sites, uint64_t n
 template <int W>
 __device__ __forceinline__ uint32_t part_of(const PKey<W>& K, const GateArg<W>& g,
                                             const PartFn<W>& f, uint32_t P) {
-    PKey<W> k;
-    if (f.pair) {
-        k = K;
-        if (f.word >= 0) {
-            const uint64_t w = f.word < W ? K.x[f.word] : K.z[f.word - W];
-            if (w & f.bit) k = key_xor(K, g);
-        }
-    } else {
+    // masks and element-wise selects only: a conditional copy of the key,
+    // or a selection of one of its words by index, puts the caller's key
+    // arrays in local memory
+    uint64_t piv = 0;
 #pragma unroll
-        for (int w = 0; w < W; ++w) { k.x[w] = K.x[w] & f.kx[w]; k.z[w] = K.z[w] & f.kz[w]; }
+    for (int v = 0; v < W; ++v) piv |= (K.x[v] & f.px[v]) | (K.z[v] & f.pz[v]);
+    const uint64_t flip = piv ? ~0ULL : 0ULL;   // pivot set: the pair key is K.Q
+    PKey<W> k;
+    if (f.pair) {   // the pair key K.Q when the pivot is set
+#pragma unroll
+        for (int v = 0; v < W; ++v) { k.x[v] = K.x[v] ^ (g.qx[v] & flip); k.z[v] = K.z[v] ^ (g.qz[v] & flip); }
+    } else {        // the key with the window's sites cleared
+#pragma unroll
+        for (int v = 0; v < W; ++v) { k.x[v] = K.x[v] & f.kx[v]; k.z[v] = K.z[v] & f.kz[v]; }
     }
     const uint64_t h = key_hash(k);   // 32 significant bits
     return (uint32_t)((h * (uint64_t)P) >> 32);
@@ -150,8 +153,8 @@ k_part_scatter(Bufs<W> B, DevCtl* ctl, PKey<W>* pk, double* pc, unsigned int* cu
         ctl->stat_scatters += 1;
         if (fallback) ctl->part_over = 1;   // the partitions hold for this gate only
     }
-    const PKey<W>* __restrict__ kin = B.k[cur];
-    const double* __restrict__ cin = B.c[cur];
+    const PKey<W>* __restrict__ kin = B.key(cur);
+    const double* __restrict__ cin = B.coef(cur);
     // a deferred top-M select: scan every stored term, keep its kept set
     const Pending<W> pd = pending_of<W>(ctl);
     uint64_t n_scan = n;
@@ -195,7 +198,7 @@ k_part_scatter(Bufs<W> B, DevCtl* ctl, PKey<W>* pk, double* pc, unsigned int* cu
                 const unsigned int pos = base + __popc(peers & lt);
                 if (pos < pl.R) {
                     const uint64_t d = (uint64_t)p * pl.R + pos;
-                    pk[d] = K[u];
+                    store_key(pk + d, K[u]);
                     pc[d] = c[u];
                 } else {
                     set_status(ctl, ST_CAPACITY, 40);
@@ -269,14 +272,17 @@ __device__ __forceinline__ uint32_t slot_hash(const PKey<W>& k) {
     return h;
 }
 
-// Shared-memory table of one partition: commuting keys and their b.
+// Shared-memory table of one partition: commuting keys and their b.  A slot
+// belongs to the partition whose tag it holds; tags grow with the partition
+// index, so a slot still tagged by an earlier partition of this CTA is free
+// and the table needs no clearing between partitions.
 template <int W>
 __device__ __forceinline__ bool part_insert(const PartItem<W>& it, PKey<W>* t_keys, double* t_b,
-                                            uint32_t* t_tag) {
+                                            uint32_t* t_tag, uint32_t tag) {
     constexpr uint32_t S = PartGeom<W>::kSlots;
     uint32_t h = slot_hash(it.K) & (S - 1);
     for (uint32_t q = 0; q < S; ++q) {
-        if (atomicCAS(t_tag + h, 0u, 1u) == 0u) {
+        if (atomicMax(t_tag + h, tag) < tag) {
             t_keys[h] = it.K;
             t_b[h] = it.b;
             return true;
@@ -288,11 +294,12 @@ __device__ __forceinline__ bool part_insert(const PartItem<W>& it, PKey<W>* t_ke
 
 template <int W>
 __device__ __forceinline__ bool part_find(const PKey<W>& P, const PKey<W>* t_keys,
-                                          const double* t_b, const uint32_t* t_tag, double* out) {
+                                          const double* t_b, const uint32_t* t_tag, uint32_t tag,
+                                          double* out) {
     constexpr uint32_t S = PartGeom<W>::kSlots;
     uint32_t h = slot_hash(P) & (S - 1);
     for (uint32_t q = 0; q < S; ++q) {
-        if (t_tag[h] == 0u) return false;
+        if (t_tag[h] != tag) return false;
         if (key_eq(t_keys[h], P)) { *out = t_b[h]; return true; }
         h = (h + 1) & (S - 1);
     }
@@ -304,10 +311,11 @@ __device__ __forceinline__ bool part_find(const PKey<W>& P, const PKey<W>* t_key
 template <int W>
 __device__ __forceinline__ void part_children(const PartItem<W>& it, const GateArg<W>& g,
                                               const PKey<W>* t_keys, const double* t_b,
-                                              const uint32_t* t_tag, double* va, bool* emit_b) {
+                                              const uint32_t* t_tag, uint32_t tag, double* va,
+                                              bool* emit_b) {
     double pb = 0.0;
     bool found = false;
-    if (it.comm) found = part_find(key_xor(it.K, g), t_keys, t_b, t_tag, &pb);
+    if (it.comm) found = part_find(key_xor(it.K, g), t_keys, t_b, t_tag, tag, &pb);
     const double a1 = __dmul_rn(it.c, g.ch);          // cosh(theta) P
     const double sum = __dadd_rn(a1, pb);             // + the partner's child
     *va = !it.comm ? it.c : (found ? sum : a1);       // {P,Q} = 0: unchanged
@@ -320,10 +328,11 @@ __device__ __forceinline__ void part_children(const PartItem<W>& it, const GateA
 template <int W>
 __device__ __forceinline__ uint32_t part_flags(const PartItem<W>& it, const GateArg<W>& g,
                                                const PKey<W>* t_keys, const double* t_b,
-                                               const uint32_t* t_tag, unsigned long long dbits,
-                                               DevCtl* ctl, int nxt, double* va) {
+                                               const uint32_t* t_tag, uint32_t tag,
+                                               unsigned long long dbits, DevCtl* ctl, int nxt,
+                                               double* va) {
     bool eb;
-    part_children(it, g, t_keys, t_b, t_tag, va, &eb);
+    part_children(it, g, t_keys, t_b, t_tag, tag, va, &eb);
     if (!it.live) return 0u;
     // threshold and weight cutoff on the merged children (Sec. II.B)
     bool keep_a = above(*va, dbits) && light(it.K, g.maxw);
@@ -384,9 +393,10 @@ __device__ __forceinline__ uint32_t scan_one_barrier(uint32_t v, uint32_t* s_war
 // commuting ones publish (key, b) in a shared-memory table, then every item
 // merges with its partner's b, and the kept children of the partition go to
 // one contiguous segment of the next state buffer, recorded as the
-// partition's descriptor for the next gate.  Four barriers per partition:
-// table built; warp totals written; segment claimed; segment written and
-// table cleared for the next partition.
+// partition's descriptor for the next gate.  Three barriers per partition:
+// table built; warp totals written; segment claimed.  The table is read only
+// before the second, so the next partition's inserts (tagged p + 1, see
+// part_insert) may start as soon as a thread has passed the third.
 template <int W, int kPBlock, int kPIpt>
 __global__ void __launch_bounds__(kPBlock, (W == 1 ? 1536 : 1024) / kPBlock)
 k_gate_part(const PKey<W>* __restrict__ pk, const double* __restrict__ pc,
@@ -414,11 +424,20 @@ k_gate_part(const PKey<W>* __restrict__ pk, const double* __restrict__ pc,
     const uint64_t R = P ? pbuf_cap / P : 0;
     const PartDesc* __restrict__ din = cur ? desc1 : desc0;
     PartDesc* __restrict__ dout = cur ? desc0 : desc1;
-    const double rnorm = ctl->rnorm[cur];
     const unsigned long long dbits = (unsigned long long)__double_as_longlong(delta);
-    const Pending<W> pd = pending_of<W>(ctl);
-    PKey<W>* __restrict__ kout = B.k[nxt];
-    double* __restrict__ cout = B.c[nxt];
+    // the normaliser and the deferred select's kept set are read from shared
+    // memory where they are applied (once per item), not held in registers
+    // through the merge
+    __shared__ Pending<W> s_pd;
+    __shared__ double s_rnorm;
+    if (threadIdx.x == 0) {
+        s_pd = pending_of<W>(ctl);
+        s_rnorm = ctl->rnorm[cur];
+    }
+    const Pending<W>& pd = s_pd;
+    const double& rnorm = s_rnorm;
+    PKey<W>* __restrict__ kout = B.key(nxt);
+    double* __restrict__ cout = B.coef(nxt);
     unsigned long long out_max = 0;   // largest |c| pattern written (top-M select range)
     for (int s2 = threadIdx.x; s2 < S; s2 += kPBlock) t_tag[s2] = 0u;
     __syncthreads();
@@ -433,8 +452,8 @@ k_gate_part(const PKey<W>* __restrict__ pk, const double* __restrict__ pc,
             cp = pc + (uint64_t)p * R;
         } else {
             np = din[p].cnt;
-            kp = B.k[cur] + din[p].off;
-            cp = B.c[cur] + din[p].off;
+            kp = B.key(cur) + din[p].off;
+            cp = B.coef(cur) + din[p].off;
         }
         // warm L2 with the partition this CTA takes next
         const uint32_t pn = p + gridDim.x;
@@ -448,8 +467,8 @@ k_gate_part(const PKey<W>* __restrict__ pk, const double* __restrict__ pc,
                 nc = reinterpret_cast<const char*>(pc + (uint64_t)pn * R);
             } else {
                 nn = din[pn].cnt;
-                nk = reinterpret_cast<const char*>(B.k[cur] + din[pn].off);
-                nc = reinterpret_cast<const char*>(B.c[cur] + din[pn].off);
+                nk = reinterpret_cast<const char*>(B.key(cur) + din[pn].off);
+                nc = reinterpret_cast<const char*>(B.coef(cur) + din[pn].off);
             }
             for (uint64_t b = (uint64_t)threadIdx.x * 128; b < nn * sizeof(PKey<W>); b += 128 * kPBlock)
                 asm volatile("prefetch.global.L2 [%0];" :: "l"(nk + b));
@@ -463,7 +482,7 @@ k_gate_part(const PKey<W>* __restrict__ pk, const double* __restrict__ pc,
 #pragma unroll
             for (int j = 0; j < kPIpt; ++j) {
                 it[j] = part_item(kp, cp, (uint64_t)j * kPBlock + threadIdx.x, np, g, rnorm, pd, ctl);
-                if (it[j].comm) ok &= part_insert(it[j], t_keys, t_b, t_tag);
+                if (it[j].comm) ok &= part_insert(it[j], t_keys, t_b, t_tag, p + 1u);
             }
             if (!ok) set_status(ctl, ST_CAPACITY, 41);
             __syncthreads();                                   // (1) table built
@@ -473,7 +492,8 @@ k_gate_part(const PKey<W>* __restrict__ pk, const double* __restrict__ pc,
             uint32_t flags = 0, cnt = 0;
 #pragma unroll
             for (int j = 0; j < kPIpt; ++j) {
-                const uint32_t fl = part_flags(it[j], g, t_keys, t_b, t_tag, dbits, ctl, nxt, &va[j]);
+                const uint32_t fl =
+                    part_flags(it[j], g, t_keys, t_b, t_tag, p + 1u, dbits, ctl, nxt, &va[j]);
                 flags |= fl << (2 * j);
                 cnt += __popc(fl);
             }
@@ -502,14 +522,12 @@ k_gate_part(const PKey<W>* __restrict__ pk, const double* __restrict__ pc,
                 out_max = max(out_max, (fl & 1u) ? abs_pattern(va[j]) : 0ULL);
                 out_max = max(out_max, (fl & 2u) ? abs_pattern(it[j].b) : 0ULL);
             }
-            for (int s2 = threadIdx.x; s2 < S; s2 += kPBlock) t_tag[s2] = 0u;
-            __syncthreads();                                   // (4) next partition
         } else {
             // a long partition: build the table, count its output, then
             // recompute and write (every item reloaded each pass)
             for (uint64_t i = threadIdx.x; i < np; i += kPBlock) {
                 const PartItem<W> x = part_item(kp, cp, i, np, g, rnorm, pd, ctl);
-                if (x.comm) ok &= part_insert(x, t_keys, t_b, t_tag);
+                if (x.comm) ok &= part_insert(x, t_keys, t_b, t_tag, p + 1u);
             }
             if (!ok) set_status(ctl, ST_CAPACITY, 41);
             if (threadIdx.x == 0) s_total = 0u;
@@ -518,7 +536,8 @@ k_gate_part(const PKey<W>* __restrict__ pk, const double* __restrict__ pc,
             for (uint64_t c0 = 0; c0 < np; c0 += kPBlock) {
                 const PartItem<W> x = part_item(kp, cp, c0 + threadIdx.x, np, g, rnorm, pd, ctl);
                 double va;
-                const uint32_t fl = part_flags(x, g, t_keys, t_b, t_tag, dbits, ctl, nxt, &va);
+                const uint32_t fl =
+                    part_flags(x, g, t_keys, t_b, t_tag, p + 1u, dbits, ctl, nxt, &va);
                 uint32_t tot;
                 block_exclusive_scan<kPBlock>(__popc(fl), &tot, s_scan);
                 if (threadIdx.x == 0) s_total += tot;
@@ -543,7 +562,8 @@ k_gate_part(const PKey<W>* __restrict__ pk, const double* __restrict__ pc,
             for (uint64_t c0 = 0; c0 < np; c0 += kPBlock) {
                 const PartItem<W> x = part_item(kp, cp, c0 + threadIdx.x, np, g, rnorm, pd, ctl);
                 double va;
-                const uint32_t fl = part_flags(x, g, t_keys, t_b, t_tag, dbits, ctl, nxt, &va);
+                const uint32_t fl =
+                    part_flags(x, g, t_keys, t_b, t_tag, p + 1u, dbits, ctl, nxt, &va);
                 uint32_t tot;
                 const uint32_t off = block_exclusive_scan<kPBlock>(__popc(fl), &tot, s_scan);
                 part_write(x, g, va, fl, kout, cout, base + run + off);
@@ -551,8 +571,7 @@ k_gate_part(const PKey<W>* __restrict__ pk, const double* __restrict__ pc,
                 out_max = max(out_max, (fl & 2u) ? abs_pattern(x.b) : 0ULL);
                 run += tot;
             }
-            for (int s2 = threadIdx.x; s2 < S; s2 += kPBlock) t_tag[s2] = 0u;
-            __syncthreads();
+            __syncthreads();   // the table is read until here
         }
     }
     // one atomic per warp for the largest pattern
@@ -591,11 +610,12 @@ static PartFn<W> part_fn_of(const HostGate& h) {
     for (int w = 0; w < W; ++w) { f.kx[w] = h.keep_x[w]; f.kz[w] = h.keep_z[w]; }
     f.pair = h.pair_mode;
     f.sites = h.win_sites;
-    f.word = -1;
-    f.bit = 0;
-    for (int w = 0; w < 2 * W && f.word < 0; ++w) {
+    bool found = false;
+    for (int w = 0; w < 2 * W; ++w) {
         const uint64_t m = w < W ? h.qx[w] : h.qz[w - W];
-        if (m) { f.word = w; f.bit = m & (~m + 1); }
+        const uint64_t bit = (!found && m) ? (m & (~m + 1)) : 0ULL;
+        if (w < W) f.px[w] = bit; else f.pz[w - W] = bit;
+        found = found || m;
     }
     return f;
 }

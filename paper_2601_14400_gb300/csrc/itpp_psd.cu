@@ -58,8 +58,8 @@ k_psd_build(Bufs<W> B, DevCtl* ctl, Slot<W>* table, uint64_t slots, int load_pct
     int probes = 0;
     for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
          i += (uint64_t)gridDim.x * blockDim.x) {
-        const PKey<W> K = load_key(B.k[cur] + i);
-        const double c = normalised(B.c[cur][i], rnorm, key_is_zero(K));
+        const PKey<W> K = load_key(B.key(cur) + i);
+        const double c = normalised(B.coef(cur)[i], rnorm, key_is_zero(K));
         if (!table_insert(table, mask, gen, K, c, (uint32_t)i, probe_limit, &probes))
             set_status(ctl, ST_HASH_PROBE, 61);
     }
@@ -90,8 +90,8 @@ k_psd_pairs(Bufs<W> B, DevCtl* ctl, const Slot<W>* table, uint64_t slots, int lo
         int probes = 0;
         for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
              i += (uint64_t)gridDim.x * blockDim.x) {
-            const PKey<W> P = load_key(B.k[cur] + i);
-            const double cp = normalised(B.c[cur][i], rnorm, key_is_zero(P));
+            const PKey<W> P = load_key(B.key(cur) + i);
+            const double cp = normalised(B.coef(cur)[i], rnorm, key_is_zero(P));
             kahan_add(den, cd, __dmul_rn(cp, cp));
             for (int j = 0; j < m; ++j) {
                 GateArg<W> o;

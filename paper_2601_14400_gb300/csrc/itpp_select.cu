@@ -119,7 +119,7 @@ k_sel_hist(Bufs<W> B, DevCtl* ctl, unsigned long long lo) {
     // the coefficients' bit patterns, read as integers (no floating point);
     // eight independent loads in flight per thread, then their counts
     const unsigned long long* __restrict__ c =
-        reinterpret_cast<const unsigned long long*>(B.c[cur]);
+        reinterpret_cast<const unsigned long long*>(B.coef(cur));
     constexpr int U = 8;
     const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
     for (uint64_t i0 = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i0 < n; i0 += U * stride) {
@@ -181,7 +181,7 @@ k_sel_gather(Bufs<W> B, DevCtl* ctl, unsigned long long lo, unsigned long long* 
     const int cur = ctl->cur;
     const uint64_t n = live_count(ctl, cur);
     const unsigned long long prefix = ctl->sel_prefix, mask = ctl->sel_mask;
-    const double* __restrict__ c = B.c[cur];
+    const double* __restrict__ c = B.coef(cur);
     constexpr int U = 4;
     const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
     if (threadIdx.x == 0) s_n = 0u;
@@ -298,7 +298,7 @@ k_sel_tcollect(Bufs<W> B, DevCtl* ctl, const unsigned long long* cand_v,
         const unsigned long long j = j0 + threadIdx.x;
         if (j < nc && cand_v[j] == T) {
             const unsigned int q = atomicAdd(&s_n, 1u);
-            st[q] = load_key(B.k[cur] + cand_idx[j]);
+            st[q] = load_key(B.key(cur) + cand_idx[j]);
         }
         __syncthreads();
         const unsigned int m = s_n;

@@ -117,8 +117,8 @@ k_sort_expand(Bufs<W> B, DevCtl* ctl, GateArg<W> g, SortBufs<W> sb, double delta
         double raw = 0.0;
         bool live = i < n, comm = false, neg = false;
         if (live) {
-            K = load_key_stream(B.k[cur] + i);
-            raw = __ldcs(B.c[cur] + i);
+            K = load_key_stream(B.key(cur) + i);
+            raw = __ldcs(B.coef(cur) + i);
             comm = commutes(K, g);
             neg = comm && product_negative(K, g);
         }
@@ -145,8 +145,8 @@ k_sort_expand(Bufs<W> B, DevCtl* ctl, GateArg<W> g, SortBufs<W> sb, double delta
             return;
         }
         if (pass) {
-            store_key_stream(B.k[cur ^ 1] + bp + off_p, K);
-            __stcs(B.c[cur ^ 1] + bp + off_p, c);
+            store_key_stream(B.key(cur ^ 1) + bp + off_p, K);
+            __stcs(B.coef(cur ^ 1) + bp + off_p, c);
         }
         if (kids) {
             const uint64_t q = bk + off_k;
@@ -330,8 +330,8 @@ k_sort_reduce(Bufs<W> B, DevCtl* ctl, SortBufs<W> sb, int src, GateArg<W> g, dou
             return;
         }
         if (keep) {
-            store_key_stream(B.k[cur ^ 1] + base + off, K);
-            __stcs(B.c[cur ^ 1] + base + off, v);
+            store_key_stream(B.key(cur ^ 1) + base + off, K);
+            __stcs(B.coef(cur ^ 1) + base + off, v);
         }
     }
 }
