@@ -53,7 +53,9 @@ typedef enum {
     ITPP_ERR_TRACE_ZERO = 6,  /* the identity coefficient was truncated or is
                                  missing, so the trace cannot be normalised         */
     ITPP_ERR_CUDA = 7,        /* a CUDA runtime call failed                         */
-    ITPP_ERR_STATE = 8        /* call not valid in the handle's current state       */
+    ITPP_ERR_STATE = 8,       /* call not valid in the handle's current state       */
+    ITPP_ERR_IO = 9           /* a state file could not be opened, read or written,
+                                 or is not a state of this handle's n             */
 } itpp_status;
 
 /* Propagation parameters.  Zero-initialise and set what you need. */
@@ -254,6 +256,40 @@ itpp_status itpp_get_terms(itpp_handle h, uint64_t* x, uint64_t* z, double* c,
  * Clears the stored device status.  Synchronising. */
 itpp_status itpp_set_terms(itpp_handle h, const uint64_t* x, const uint64_t* z,
                            const double* c, uint64_t count);
+
+/* Sort count terms held in host arrays into the canonical order: ascending
+ * by x word 0, x word 1, ..., then z word 0, z word 1, ... (unsigned 64-bit
+ * comparisons), the (x, z, c) triple of a term moving together.  This is the
+ * order in which exported states are compared term by term.  Equal keys keep
+ * an unspecified relative order (a state has none).  Runs on the host only:
+ * no handle, no device.  x, z: count * W words each, c: count doubles, all
+ * in place.  Errors: ITPP_ERR_ARG (W not 1 or 2; a NULL array with
+ * count > 0), ITPP_ERR_ALLOC (the host scratch, 8 + 16W bytes a term). */
+itpp_status itpp_sort_terms(int W, uint64_t* x, uint64_t* z, double* c, uint64_t count);
+
+/* itpp_get_terms, then itpp_sort_terms on the copied terms: the normalised
+ * state in the canonical order.  Arguments and errors as itpp_get_terms
+ * (plus ITPP_ERR_ALLOC).  Synchronising. */
+itpp_status itpp_get_terms_sorted(itpp_handle h, uint64_t* x, uint64_t* z, double* c,
+                                  uint64_t capacity, uint64_t* count);
+
+/* Checkpoint the normalised state to a file (resume with itpp_load).  The
+ * file holds, little-endian: the 8 bytes "ITPPST01", int32 n, int32 W,
+ * uint64 count, then the x words (count * W uint64), the z words (same)
+ * and the coefficients (count doubles), terms in the canonical order of
+ * itpp_sort_terms, so equal states give equal files.  path: host string.
+ * Errors: ITPP_ERR_ARG (NULL handle or path), ITPP_ERR_IO, ITPP_ERR_ALLOC,
+ * the handle's stored error.  Synchronising. */
+itpp_status itpp_save(itpp_handle h, const char* path);
+
+/* Replace the state by the one a file written by itpp_save holds (the same
+ * n is required; the gates, dtau and parameters stay those of h), as
+ * itpp_set_terms does; continuing from a loaded state gives the same terms
+ * and coefficients, bit for bit, as continuing the saved handle.  Errors:
+ * ITPP_ERR_ARG (NULL arguments), ITPP_ERR_IO (unreadable, truncated, wrong
+ * magic, another n or W, more than cap_M terms), the errors of
+ * itpp_set_terms.  Synchronising. */
+itpp_status itpp_load(itpp_handle h, const char* path);
 
 /* Device counters (see itpp_stats).  Synchronising. */
 itpp_status itpp_get_stats(itpp_handle h, itpp_stats* out);

@@ -26,7 +26,7 @@ _vp = ctypes.c_void_p
 ITPP_OK = 0
 STATUS_NAMES = {0: "ok", 1: "ERR_ARG", 2: "ERR_ALLOC", 3: "ERR_CAPACITY",
                 4: "ERR_HASH_PROBE", 5: "ERR_TIMEOUT", 6: "ERR_TRACE_ZERO",
-                7: "ERR_CUDA", 8: "ERR_STATE"}
+                7: "ERR_CUDA", 8: "ERR_STATE", 9: "ERR_IO"}
 
 
 class itpp_params(ctypes.Structure):
@@ -79,6 +79,10 @@ _SIGNATURES = [
     ("itpp_get_count", ctypes.c_int, [_vp, _u64p]),
     ("itpp_get_terms", ctypes.c_int, [_vp, _u64p, _u64p, _f64p, ctypes.c_uint64, _u64p]),
     ("itpp_set_terms", ctypes.c_int, [_vp, _u64p, _u64p, _f64p, ctypes.c_uint64]),
+    ("itpp_sort_terms", ctypes.c_int, [ctypes.c_int, _u64p, _u64p, _f64p, ctypes.c_uint64]),
+    ("itpp_get_terms_sorted", ctypes.c_int, [_vp, _u64p, _u64p, _f64p, ctypes.c_uint64, _u64p]),
+    ("itpp_save", ctypes.c_int, [_vp, ctypes.c_char_p]),
+    ("itpp_load", ctypes.c_int, [_vp, ctypes.c_char_p]),
     ("itpp_get_stats", ctypes.c_int, [_vp, ctypes.POINTER(itpp_stats)]),
     ("itpp_profile_enable", ctypes.c_int, [_vp, ctypes.c_int]),
     ("itpp_profile_read", ctypes.c_int, [_vp, ctypes.c_int, _u64p, _f64p]),
@@ -145,6 +149,18 @@ def itpp_gate_apply_noalloc(n, gate_x, gate_z, alpha, dtau, delta, d_keys_in, d_
                                        d_keys_out, d_coef_out, int(out_capacity), d_n_out,
                                        d_trace_out, _stream_ptr(stream))
     _check(st, "itpp_gate_apply_noalloc")
+
+
+def sort_terms(x, z, c):
+    """Copies of host arrays (x[count, W], z[count, W], c[count]) sorted into
+    the canonical order by itpp_sort_terms."""
+    x = np.array(x, dtype=np.uint64, order="C", copy=True)
+    z = np.array(z, dtype=np.uint64, order="C", copy=True)
+    c = np.array(c, dtype=np.float64, order="C", copy=True)
+    W = x.shape[1] if x.ndim == 2 else 1
+    _check(lib().itpp_sort_terms(W, x.ctypes.data_as(_u64p), z.ctypes.data_as(_u64p),
+                                 c.ctypes.data_as(_f64p), int(c.shape[0])), "itpp_sort_terms")
+    return x, z, c
 
 
 def _u64(a):
@@ -255,11 +271,25 @@ class Propagator:
         return x, z, c
 
     def sorted_terms(self):
-        """Terms in ascending key order (x words, then z words)."""
-        x, z, c = self.terms()
-        order = np.lexsort(tuple(z[:, w] for w in range(self.W - 1, -1, -1)) +
-                           tuple(x[:, w] for w in range(self.W - 1, -1, -1)))
-        return x[order], z[order], c[order]
+        """Terms in the canonical order (ascending: x words, then z words),
+        from itpp_get_terms_sorted."""
+        n = self.count()
+        x = np.zeros((n, self.W), dtype=np.uint64)
+        z = np.zeros((n, self.W), dtype=np.uint64)
+        c = np.zeros(n)
+        got = ctypes.c_uint64()
+        _check(lib().itpp_get_terms_sorted(self._h, x.ctypes.data_as(_u64p),
+                                           z.ctypes.data_as(_u64p), c.ctypes.data_as(_f64p),
+                                           n, ctypes.byref(got)), "itpp_get_terms_sorted")
+        return x, z, c
+
+    def save(self, path):
+        """Checkpoint the state to a file (see itpp_save)."""
+        _check(lib().itpp_save(self._h, os.fsencode(path)), "itpp_save")
+
+    def load(self, path):
+        """Replace the state by a checkpoint written by save (see itpp_load)."""
+        _check(lib().itpp_load(self._h, os.fsencode(path)), "itpp_load")
 
     def set_terms(self, x, z, c):
         x, px = _u64(x)

@@ -2,8 +2,10 @@
 // per-gate weights, launch ordering, synchronising reads.  No step of the
 // propagation itself runs here; every one is a kernel in itpp_gate.cu /
 // itpp_aux.cu.
+#include <algorithm>
 #include <cmath>
 #include <cstddef>
+#include <cstdio>
 #include <cstring>
 #include <new>
 #include <vector>
@@ -209,6 +211,58 @@ itpp_status check_obs_args(itpp_ctx* h, const uint64_t* ox, const uint64_t* oz, 
 itpp_status itpp_detail_sync_ctl(itpp_ctx* h) { return sync_ctl(h); }
 itpp_status itpp_detail_launch_gate(itpp_ctx* h, int k) { return launch_one_gate(h, k); }
 
+// ---------------------------------------------------------------------------
+// Canonical order and checkpoints (host side)
+// ---------------------------------------------------------------------------
+namespace {
+
+template <int W>
+struct HostTerm {
+    uint64_t k[2 * W];   // x words, then z words: the comparison order
+    double c;
+};
+
+template <int W>
+itpp_status sort_terms_w(uint64_t* x, uint64_t* z, double* c, uint64_t count) {
+    std::vector<HostTerm<W>> t;
+    try {
+        t.resize(count);
+    } catch (...) {
+        return ITPP_ERR_ALLOC;
+    }
+    for (uint64_t i = 0; i < count; ++i) {
+        for (int w = 0; w < W; ++w) {
+            t[i].k[w] = x[i * W + w];
+            t[i].k[W + w] = z[i * W + w];
+        }
+        t[i].c = c[i];
+    }
+    std::sort(t.begin(), t.end(), [](const HostTerm<W>& a, const HostTerm<W>& b) {
+        for (int w = 0; w < 2 * W; ++w)
+            if (a.k[w] != b.k[w]) return a.k[w] < b.k[w];
+        return false;
+    });
+    for (uint64_t i = 0; i < count; ++i) {
+        for (int w = 0; w < W; ++w) {
+            x[i * W + w] = t[i].k[w];
+            z[i * W + w] = t[i].k[W + w];
+        }
+        c[i] = t[i].c;
+    }
+    return ITPP_OK;
+}
+
+constexpr char kStateMagic[8] = {'I', 'T', 'P', 'P', 'S', 'T', '0', '1'};
+
+struct FileCloser {
+    FILE* f;
+    ~FileCloser() {
+        if (f) fclose(f);
+    }
+};
+
+}  // namespace
+
 extern "C" {
 
 const char* itpp_status_string(itpp_status s) {
@@ -222,6 +276,7 @@ const char* itpp_status_string(itpp_status s) {
         case ITPP_ERR_TRACE_ZERO: return "identity coefficient truncated or missing";
         case ITPP_ERR_CUDA: return "CUDA runtime error";
         case ITPP_ERR_STATE: return "invalid state";
+        case ITPP_ERR_IO: return "state file unreadable, unwritable or of another size";
     }
     return "unknown status";
 }
@@ -458,6 +513,79 @@ itpp_status itpp_get_terms(itpp_handle h, uint64_t* x, uint64_t* z, double* c,
         cudaMemcpyAsync(c, dc, (size_t)n * 8, cudaMemcpyDeviceToHost, h->stream) != cudaSuccess)
         return cuda_fail(h);
     return sync_ctl(h);
+}
+
+itpp_status itpp_sort_terms(int W, uint64_t* x, uint64_t* z, double* c, uint64_t count) {
+    if (W != 1 && W != 2) return ITPP_ERR_ARG;
+    if (count == 0) return ITPP_OK;
+    if (!x || !z || !c) return ITPP_ERR_ARG;
+    return W == 1 ? sort_terms_w<1>(x, z, c, count) : sort_terms_w<2>(x, z, c, count);
+}
+
+itpp_status itpp_get_terms_sorted(itpp_handle h, uint64_t* x, uint64_t* z, double* c,
+                                  uint64_t capacity, uint64_t* count) {
+    itpp_status st = itpp_get_terms(h, x, z, c, capacity, count);
+    if (st) return st;
+    return itpp_sort_terms(h->s.W, x, z, c, *count);
+}
+
+itpp_status itpp_save(itpp_handle h, const char* path) {
+    if (!h || !path) return ITPP_ERR_ARG;
+    uint64_t n = 0;
+    itpp_status st = itpp_get_count(h, &n);
+    if (st) return st;
+    const int W = h->s.W;
+    std::vector<uint64_t> x, z;
+    std::vector<double> c;
+    try {
+        x.resize(n * W);
+        z.resize(n * W);
+        c.resize(n);
+    } catch (...) {
+        return ITPP_ERR_ALLOC;
+    }
+    uint64_t got = 0;
+    st = itpp_get_terms_sorted(h, x.data(), z.data(), c.data(), n, &got);
+    if (st) return st;
+    FileCloser fc{fopen(path, "wb")};
+    if (!fc.f) return ITPP_ERR_IO;
+    const int32_t hdr[2] = {h->s.n, W};
+    bool ok = fwrite(kStateMagic, 1, 8, fc.f) == 8 && fwrite(hdr, 4, 2, fc.f) == 2 &&
+              fwrite(&got, 8, 1, fc.f) == 1 &&
+              fwrite(x.data(), 8, got * W, fc.f) == got * W &&
+              fwrite(z.data(), 8, got * W, fc.f) == got * W &&
+              fwrite(c.data(), 8, got, fc.f) == got;
+    ok = fclose(fc.f) == 0 && ok;
+    fc.f = nullptr;
+    return ok ? ITPP_OK : ITPP_ERR_IO;
+}
+
+itpp_status itpp_load(itpp_handle h, const char* path) {
+    if (!h || !path) return ITPP_ERR_ARG;
+    FileCloser fc{fopen(path, "rb")};
+    if (!fc.f) return ITPP_ERR_IO;
+    char magic[8];
+    int32_t hdr[2];
+    uint64_t count = 0;
+    if (fread(magic, 1, 8, fc.f) != 8 || memcmp(magic, kStateMagic, 8) != 0 ||
+        fread(hdr, 4, 2, fc.f) != 2 || fread(&count, 8, 1, fc.f) != 1)
+        return ITPP_ERR_IO;
+    const int W = h->s.W;
+    if (hdr[0] != h->s.n || hdr[1] != W || count < 1 || count > h->s.cap_M) return ITPP_ERR_IO;
+    std::vector<uint64_t> x, z;
+    std::vector<double> c;
+    try {
+        x.resize(count * W);
+        z.resize(count * W);
+        c.resize(count);
+    } catch (...) {
+        return ITPP_ERR_ALLOC;
+    }
+    if (fread(x.data(), 8, count * W, fc.f) != count * W ||
+        fread(z.data(), 8, count * W, fc.f) != count * W ||
+        fread(c.data(), 8, count, fc.f) != count)
+        return ITPP_ERR_IO;
+    return itpp_set_terms(h, x.data(), z.data(), c.data(), count);
 }
 
 itpp_status itpp_set_terms(itpp_handle h, const uint64_t* x, const uint64_t* z, const double* c,
