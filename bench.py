@@ -149,41 +149,70 @@ class ClockSampler:
 
 
 def dist_init():
+    """One process per GPU under torchrun (NCCL); gloo where no GPU is
+    visible, which is how the host-side aggregation is tested on a CPU."""
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
     if world > 1:
+        import torch
         import torch.distributed as dist
-        backend = "nccl"
-        dist.init_process_group(backend=backend)
+        dist.init_process_group(backend="nccl" if torch.cuda.is_available() else "gloo")
     return world, rank, local
+
+
+def _on_nccl():
+    import torch.distributed as dist
+    return dist.get_backend() == "nccl"
 
 
 def barrier(world):
     if world > 1:
         import torch
         import torch.distributed as dist
-        dist.barrier(device_ids=[torch.cuda.current_device()])
+        if _on_nccl():
+            dist.barrier(device_ids=[torch.cuda.current_device()])
+        else:
+            dist.barrier()
+
+
+def _all_reduce(world, v, op):
+    if world == 1:
+        return v
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([v], dtype=torch.float64, device="cuda" if _on_nccl() else "cpu")
+    dist.all_reduce(t, op=op)
+    return float(t.item())
 
 
 def max_over_ranks(world, v):
-    if world == 1:
-        return v
-    import torch
     import torch.distributed as dist
-    t = torch.tensor([v], dtype=torch.float64, device="cuda")
-    dist.all_reduce(t, op=dist.ReduceOp.MAX)
-    return float(t.item())
+    return v if world == 1 else _all_reduce(world, v, dist.ReduceOp.MAX)
 
 
 def sum_over_ranks(world, v):
-    if world == 1:
-        return v
-    import torch
     import torch.distributed as dist
-    t = torch.tensor([v], dtype=torch.float64, device="cuda")
-    dist.all_reduce(t, op=dist.ReduceOp.SUM)
-    return float(t.item())
+    return v if world == 1 else _all_reduce(world, v, dist.ReduceOp.SUM)
+
+
+def replica_throughput(world, units, ms):
+    """Whole-job throughput of independent replicas: the units every rank
+    processed over the slowest rank's time.  Returns (value per second,
+    total units, max ms)."""
+    ms_max = max_over_ranks(world, float(ms))
+    total = sum_over_ranks(world, float(units))
+    return total / (ms_max * 1e-3), total, ms_max
+
+
+def static_config(w, world):
+    """The workload description both arms print."""
+    return {"workload": w.name, "n": w.H.n, "mask_words": w.H.W, "dtau": w.dtau,
+            "delta": w.delta, "cap_M": w.cap_M,
+            "cap_policy": "top-M" if w.cap_policy else "error",
+            "gates_per_step": w.H.n_gates,
+            "l2": "state larger than L2 (no flush)",
+            "parallelism": f"replicas x{world}"}
 
 
 # ---------------------------------------------------------------------------
@@ -225,7 +254,7 @@ def run_reference(args, w):
             "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": 1e3 * tot_t / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": w.name},
+            "config": static_config(w, world),
             "cpu_baseline": {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle",
                              "sample": sample},
             "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
@@ -503,9 +532,7 @@ def main():
     terms_out = st1["terms_out"] - st0["terms_out"]
     gates = st1["gates_applied"] - st0["gates_applied"]
     launches = st1["kernel_launches"] - st0["kernel_launches"]
-    ms_max = max_over_ranks(world, ms)
-    total_terms = sum_over_ranks(world, float(terms_in))
-    value = total_terms / (ms_max * 1e-3)
+    value, total_terms, ms_max = replica_throughput(world, terms_in, ms)
 
     # roofline of the dominant kernel class and of the whole gate
     peak, peak_kind = load_peaks()
@@ -577,13 +604,8 @@ def main():
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_max / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic",
-            "config": {"workload": w.name, "n": w.H.n, "mask_words": W,
-                       "dtau": w.dtau, "delta": w.delta, "cap_M": w.cap_M,
-                       "cap_policy": "top-M" if w.cap_policy else "error",
-                       "gates_per_step": w.H.n_gates, "setup_layers": setup,
-                       "terms_at_start": st0["count"],
-                       "l2": "state larger than L2 (no flush)",
-                       "parallelism": f"replicas x{world}"},
+            "config": dict(static_config(w, world), setup_layers=setup,
+                           terms_at_start=st0["count"]),
             "roofline": {"bound": "hbm", "kernel": KERNEL_NAMES[args.merge_path][dom],
                          "achieved": achieved_dom, "peak": peak, "unit": "GB/s",
                          "frac": achieved_dom / peak, "traffic": traffic,
