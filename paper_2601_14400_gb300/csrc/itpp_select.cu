@@ -164,8 +164,14 @@ k_sel_hist(Bufs<W> B, DevCtl* ctl, unsigned long long lo) {
 }
 
 // ---------------------------------------------------------------------------
-// 2. Candidates: the terms of the threshold's first digit.  A CTA stages
-// them in shared memory and claims global space once per flush.
+// 2. Candidates: the terms of the threshold's first digit.  A warp claims
+// room for its hits in the CTA's shared stage (one shared atomic per warp and
+// load round that has hits, no block barrier in the loop); once the stage is
+// full, later hits go straight to the global list.  The successful claims
+// form a prefix of the stage (after the first claim that does not fit, every
+// later one starts past the end), which the CTA copies out at the end with
+// one global claim.  The order of the candidates is immaterial: every later
+// pass histograms them and the ties are sorted by key.
 // ---------------------------------------------------------------------------
 constexpr int kStage = 3072;      // staged candidates per CTA (36 KB)
 
@@ -175,34 +181,22 @@ k_sel_gather(Bufs<W> B, DevCtl* ctl, unsigned long long lo, unsigned long long* 
              uint32_t* cand_idx, uint64_t cand_cap) {
     __shared__ unsigned long long st_v[kStage];
     __shared__ uint32_t st_i[kStage];
-    __shared__ unsigned int s_n;
+    __shared__ unsigned int s_claimed, s_staged;
     __shared__ unsigned long long s_base;
     if (!ctl->sel_active || ctl->status) return;
     const int cur = ctl->cur;
     const uint64_t n = live_count(ctl, cur);
     const unsigned long long prefix = ctl->sel_prefix, mask = ctl->sel_mask;
     const double* __restrict__ c = B.coef(cur);
-    constexpr int U = 4;
+    constexpr int U = 8;
     const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
-    if (threadIdx.x == 0) s_n = 0u;
+    const unsigned int lane = threadIdx.x & 31u, lt = (1u << lane) - 1u;
+    if (threadIdx.x == 0) {
+        s_claimed = 0u;
+        s_staged = 0u;
+    }
     __syncthreads();
-    auto flush = [&]() {
-        const unsigned int m = s_n;
-        if (threadIdx.x == 0) s_base = m ? atomicAdd(&ctl->sel_cand_n, (unsigned long long)m) : 0ULL;
-        __syncthreads();
-        const unsigned long long base = s_base;
-        for (unsigned int j = threadIdx.x; j < m; j += blockDim.x) {
-            if (base + j < cand_cap) {
-                cand_v[base + j] = st_v[j];
-                cand_idx[base + j] = st_i[j];
-            } else {
-                set_status(ctl, ST_CAPACITY, 30);
-            }
-        }
-        __syncthreads();
-        if (threadIdx.x == 0) s_n = 0u;
-        __syncthreads();
-    };
+    // whole warps iterate together (the claims below are warp-wide)
     for (uint64_t i0 = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
          i0 - threadIdx.x < n; i0 += U * stride) {
         double v[U];
@@ -215,17 +209,48 @@ k_sel_gather(Bufs<W> B, DevCtl* ctl, unsigned long long lo, unsigned long long* 
         for (int u = 0; u < U; ++u) {
             const uint64_t i = i0 + (uint64_t)u * stride;
             const unsigned long long x = sel_value(v[u], lo);
-            if (i < n && (x & mask) == prefix) {
-                const unsigned int q = atomicAdd(&s_n, 1u);
-                st_v[q] = x;
-                st_i[q] = (uint32_t)i;
+            const bool hit = i < n && (x & mask) == prefix;
+            const unsigned int b = __ballot_sync(0xffffffffu, hit);
+            if (!b) continue;                                   // warp-uniform
+            const int leader = __ffs(b) - 1;
+            const unsigned int nb = __popc(b), r = __popc(b & lt);
+            unsigned int q = 0u;
+            if ((int)lane == leader) q = atomicAdd(&s_claimed, nb);
+            q = __shfl_sync(0xffffffffu, q, leader);
+            if (q + nb <= (unsigned int)kStage) {               // warp-uniform
+                if (hit) {
+                    st_v[q + r] = x;
+                    st_i[q + r] = (uint32_t)i;
+                }
+                if ((int)lane == leader) atomicAdd(&s_staged, nb);
+            } else {
+                unsigned long long g = 0ULL;
+                if ((int)lane == leader) g = atomicAdd(&ctl->sel_cand_n, (unsigned long long)nb);
+                g = __shfl_sync(0xffffffffu, g, leader);
+                if (hit) {
+                    if (g + r < cand_cap) {
+                        cand_v[g + r] = x;
+                        cand_idx[g + r] = (uint32_t)i;
+                    } else {
+                        set_status(ctl, ST_CAPACITY, 30);
+                    }
+                }
             }
         }
-        __syncthreads();
-        if (s_n > kStage - U * 256) flush();
     }
     __syncthreads();
-    flush();
+    const unsigned int m = s_staged;
+    if (threadIdx.x == 0) s_base = m ? atomicAdd(&ctl->sel_cand_n, (unsigned long long)m) : 0ULL;
+    __syncthreads();
+    const unsigned long long base = s_base;
+    for (unsigned int j = threadIdx.x; j < m; j += blockDim.x) {
+        if (base + j < cand_cap) {
+            cand_v[base + j] = st_v[j];
+            cand_idx[base + j] = st_i[j];
+        } else {
+            set_status(ctl, ST_CAPACITY, 30);
+        }
+    }
 }
 
 // ---------------------------------------------------------------------------

@@ -217,6 +217,29 @@ def test_cap_policy_topM_with_exact_ties():
     assert_same_state(g.terms(), o.terms(), "ties")
 
 
+@pytest.mark.parametrize("cap_M", [4_000_001, 4_500_000])
+def test_cap_policy_topM_large_tie_class(cap_M):
+    # 4M strings with |c| = 1/2: after a ZZ gate about 2M children share
+    # each of three magnitudes, so the first digit of the select holds about
+    # 2M candidates, more than the gather's shared stages hold (the overflow
+    # path writes them straight to the list).  cap_M = 4M + 1 keeps exactly
+    # the two upper classes; 4.5M cuts inside the third, where the key
+    # tie-break decides among 2M equal magnitudes.
+    n, M = 64, 4_000_000
+    X, Z, C = wl.synthetic_state(n, M, 1461, delta=1e-6)
+    C[1:] = np.where(C[1:] < 0, -0.5, 0.5)
+    gx, gz = wl.two_site(n, 10, 11, "Z", "Z")
+    H = wl.Hamiltonian(n, gx[None], gz[None], np.array([-1.0]))
+    g, o = _pair(H, 0.1, 1e-12, cap_M=cap_M, cap_policy=1)
+    g.set_terms(X, Z, C)
+    o.set_terms(X, Z, C)
+    g.apply_gate(0)
+    o.apply_gate(0)
+    st = g.stats()
+    assert st["select_candidates"] > 1_900_000 and st["cap_events"] == 1
+    assert_same_state(g.terms(), o.terms(), f"cap_M={cap_M}")
+
+
 def test_set_terms_validation():
     H = wl.tfim_1d(8, 1.0, 1.0)
     g = itpp.Propagator(H.n, H.gate_x, H.gate_z, H.alpha, 0.1, 1e-9, 1000, 0)
