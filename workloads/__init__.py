@@ -315,6 +315,49 @@ def synthetic_state(n: int, M: int, seed: int, delta: float = 1e-6):
     return X, Z, C
 
 
+def paired_state(n_base: int, seed: int, pair_zbits: int, pair_every: int = 2,
+                 delta: float = 1e-6):
+    """A large n = 64 state with a known pair structure, built without any
+    deduplication (full-size single-gate checks).
+
+    Base string j (j = 1..n_base): x = j * A mod 2^64 with A odd, so the x
+    words alone are distinct and nonzero; z = j * B + D mod 2^64 with the bits
+    of ``pair_zbits`` cleared.  Every ``pair_every``-th base string (j a
+    multiple of it) also appears with those z bits set: the two rows differ
+    only there, and no other row shares their x word.  Coefficients: sign
+    uniform, ``|c|`` log-uniform in ``[delta, 1]``; the identity (c = 1) is
+    row 0.  Returns ``(x, z, c, base_row, pair_row)``: x, z of shape
+    ``(N, 1)``, and for base string j (index j - 1) its row and its pair's
+    row (-1 when absent).
+    """
+    rng = np.random.default_rng(seed)
+    A = np.uint64(0x9E3779B97F4A7C15)
+    B = np.uint64(0xC2B2AE3D27D4EB4F)
+    D = np.uint64(0x165667B19E3779F9)
+    j = np.arange(1, n_base + 1, dtype=np.uint64)
+    with np.errstate(over="ignore"):
+        bx = j * A
+        bz = (j * B + D) & ~np.uint64(pair_zbits)
+    paired = (j % np.uint64(pair_every)) == 0
+    n_pair = int(paired.sum())
+    N = 1 + n_base + n_pair
+    X = np.zeros((N, 1), dtype=np.uint64)
+    Z = np.zeros((N, 1), dtype=np.uint64)
+    X[1:n_base + 1, 0] = bx
+    Z[1:n_base + 1, 0] = bz
+    X[n_base + 1:, 0] = bx[paired]
+    Z[n_base + 1:, 0] = bz[paired] | np.uint64(pair_zbits)
+    base_row = np.arange(1, n_base + 1, dtype=np.int64)
+    pair_row = np.full(n_base, -1, dtype=np.int64)
+    pair_row[paired] = np.arange(n_base + 1, N, dtype=np.int64)
+    mag = np.exp(rng.uniform(math.log(delta), 0.0, N - 1))
+    sgn = np.where(rng.integers(0, 2, N - 1) == 1, 1.0, -1.0)
+    C = np.empty(N)
+    C[0] = 1.0
+    C[1:] = sgn * mag
+    return X, Z, C, base_row, pair_row
+
+
 # --------------------------------------------------------------------------
 # The workloads the library is measured and checked on.
 # --------------------------------------------------------------------------
