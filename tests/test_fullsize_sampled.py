@@ -121,3 +121,25 @@ def test_full_size_gate_on_sampled_strings():
     expected, cand = _oracle_on_sample(X, Z, C, base_row, pair_row, 20000, 11)
     kept, cut, absent = _check(got, FULL_M, expected, cand)
     assert kept > 15000 and cut > 100 and absent > 100
+
+
+def test_paired_state_structure():
+    # the generator's promises the full-size check relies on, on a medium size
+    n_base = 200_000
+    X, Z, C, base_row, pair_row = wl.paired_state(n_base, 3, PAIR_ZBITS)
+    N = X.shape[0]
+    assert N == 1 + n_base + n_base // 2
+    assert X[0, 0] == 0 and Z[0, 0] == 0 and C[0] == 1.0
+    x, z = X[1:, 0], Z[1:, 0]
+    assert np.all(x != 0)                                     # no second identity
+    keys = np.stack([x, z], axis=1)
+    assert np.unique(keys, axis=0).shape[0] == N - 1          # distinct strings
+    bx = X[base_row, 0]
+    assert np.unique(bx).shape[0] == n_base                   # x words distinct
+    assert np.all(Z[base_row, 0] & np.uint64(PAIR_ZBITS) == 0)
+    has = pair_row >= 0
+    assert has.sum() == n_base // 2
+    assert np.array_equal(X[pair_row[has], 0], bx[has])
+    assert np.array_equal(Z[pair_row[has], 0], Z[base_row[has], 0] | np.uint64(PAIR_ZBITS))
+    mags = np.abs(C[1:])
+    assert mags.min() >= 1e-6 and mags.max() <= 1.0
