@@ -49,5 +49,6 @@ def test_tfim_2d_order_and_signs():
     for i in range(n):
         assert _letters(H, 220 + i) == [(i, "X")]
         assert H.alpha[220 + i] == -3.04
-    assert H.W == 2                                                   # bits >= 121 clear
-    assert np.all(H.gate_x[:, 1] >> np.uint64(57) == 0) and np.all(H.gate_z[:, 1] >> np.uint64(57) == 0)
+    assert H.W == 2
+    top = np.uint64(121 - 64)          # bits >= 121 of the second word are clear
+    assert np.all(H.gate_x[:, 1] >> top == 0) and np.all(H.gate_z[:, 1] >> top == 0)
