@@ -72,9 +72,12 @@ def parse():
                     help="mean partition size of the partitioned merge (0: library default)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
-    ap.add_argument("--mode", default="headline", choices=["headline", "batch", "adjoint", "synth"],
+    ap.add_argument("--mode", default="headline",
+                    choices=["headline", "batch", "adjoint", "synth", "variants"],
                     help="headline: the metric line; batch / adjoint: the extension "
-                         "timings against plain single-instance runs")
+                         "timings against plain single-instance runs; variants: the "
+                         "Strang schedule, the weight cutoff, K-truncation and the "
+                         "PSD-restored observable on the headline workload")
     ap.add_argument("--batch-cap-log2", type=int, default=16)
     ap.add_argument("--synth-sizes", default="20,23,26",
                     help="log2 of the synthetic state sizes (--mode synth)")
@@ -380,6 +383,70 @@ def run_synth(args):
     return 0
 
 
+def run_variants(args):
+    """The propagation variants on the headline workload (n = 64 periodic
+    chain, its bound and top-M select), each grown to the bound untimed and
+    then timed over --steps layers with CUDA events on the library stream:
+    the first-order product, the Strang product (2G - 1 gates per layer),
+    the Pauli weight cutoff (weight <= 8) and K-truncation (delta = 0).  On
+    the first-order state at the bound: the PSD-restored observable for
+    <Z0 Z1> and for the energy, timed with events."""
+    import torch
+    import paper_2601_14400_gb300 as itpp
+    if not os.path.exists(itpp.LIB_PATH):
+        itpp.build()
+    w = wl.WORKLOADS[args.workload]
+    M = 1 << args.cap_log2 if args.cap_log2 else w.cap_M
+    stream = torch.cuda.Stream()
+    points, psd = [], []
+    for name, kw, delta in (("first order", {}, w.delta),
+                            ("Strang", {"trotter_order": 2}, w.delta),
+                            ("weight <= 8", {"max_weight": 8}, w.delta),
+                            ("K-truncation", {}, 0.0)):
+        g = itpp.Propagator(w.H.n, w.H.gate_x, w.H.gate_z, w.H.alpha, w.dtau, delta, M, 1,
+                            stream=stream, **kw)
+        setup = 0
+        while setup < 40 and g.count() < M:
+            g.apply_trotter_layer(1)
+            setup += 1
+        g.apply_trotter_layer(max(args.warmup, 1))
+        g.synchronize()
+        st0 = g.stats()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        g.apply_trotter_layer(args.steps)
+        e1.record(stream)
+        g.synchronize()
+        ms = e0.elapsed_time(e1)
+        st1 = g.stats()
+        terms = st1["terms_in"] - st0["terms_in"]
+        gates = st1["gates_applied"] - st0["gates_applied"]
+        points.append({"variant": name, "setup_layers": setup, "terms_at_end": g.count(),
+                       "terms_per_s": terms / (ms * 1e-3), "gate_ms": ms / max(gates, 1),
+                       "gates_per_layer": gates // max(args.steps, 1)})
+        if name == "first order":
+            for label, obs in (("Z0Z1", w.observables["Z0Z1"]),
+                               ("energy", w.observables["energy"])):
+                g.expect_psd(obs)                       # warm-up (tables, scratch)
+                g.synchronize()
+                e0.record(stream)
+                val = g.expect_psd(obs)
+                e1.record(stream)
+                g.synchronize()
+                t = e0.elapsed_time(e1)
+                psd.append({"observable": label, "strings": int(obs.w.shape[0]),
+                            "ms": t, "terms_per_s": g.count() / (t * 1e-3),
+                            "value": val[0]})
+        g.close()
+        torch.cuda.synchronize()
+    line = {"metric": "propagation variants: Pauli terms/s per Trotter gate", "mode": "variants",
+            "unit": UNIT, "points": points, "psd": psd, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": w.name, "cap_M": M, "cap_policy": "top-M",
+                       "timed_layers": args.steps}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def run_adjoint(args):
     """n = 32 open chain with per-site fields and couplings (63 parameters),
     dtau = 0.02, 50 layers, |c| <= 1e-7 dropped: the energy and <Z15 Z16>
@@ -466,6 +533,8 @@ def main():
         return run_adjoint(args)
     if args.mode == "synth":
         return run_synth(args)
+    if args.mode == "variants":
+        return run_variants(args)
     w = wl.WORKLOADS[args.workload]
     if args.cap_log2:
         w.cap_M = 1 << args.cap_log2
