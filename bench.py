@@ -73,7 +73,7 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--mode", default="headline",
-                    choices=["headline", "batch", "adjoint", "synth", "variants"],
+                    choices=["headline", "batch", "adjoint", "synth", "variants", "kscan"],
                     help="headline: the metric line; batch / adjoint: the extension "
                          "timings against plain single-instance runs; variants: the "
                          "Strang schedule, the weight cutoff, K-truncation and the "
@@ -86,6 +86,17 @@ def parse():
     ap.add_argument("--batch-layers", type=int, default=5)
     ap.add_argument("--ref-gates", type=int, default=224,
                     help="oracle gates per reference step (bounded CPU sample)")
+    ap.add_argument("--no-extras", action="store_true",
+                    help="headline only: skip layers_by_beta, cfg3, adjoint_vs_plain and "
+                         "batch_vs_plain")
+    ap.add_argument("--beta-marks", default="20,50,100,150,200",
+                    help="layers of the headline run timed after the timed region")
+    ap.add_argument("--extra-batch-layers", type=int, default=50)
+    ap.add_argument("--extra-batch-cap-log2", type=int, default=18)
+    ap.add_argument("--cfg3-layers", type=int, default=2)
+    ap.add_argument("--kscan-betas", default="0.08,0.24,0.8")
+    ap.add_argument("--kscan-budget", type=float, default=900.0,
+                    help="seconds of the K-truncation scan (--mode kscan)")
     return ap.parse_args()
 
 
@@ -259,7 +270,11 @@ def run_reference(args, w):
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": static_config(w, world),
             "cpu_baseline": {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle",
-                             "sample": sample},
+                             "sample": sample,
+                             "config": {"workload": w.name, "gates": args.ref_gates,
+                                        "from": "the identity",
+                                        "note": "the same workload's first gates (small "
+                                                "states), not its 2^26-term bound"}},
             "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
     return 0
@@ -268,24 +283,23 @@ def run_reference(args, w):
 # ---------------------------------------------------------------------------
 # GPU arm
 # ---------------------------------------------------------------------------
-def run_batch(args):
-    """64 independent open chains (n ~ U{16..64}, h ~ U[0.5, 2], J = 1,
-    dtau = 0.02, delta = 1e-7, at most 2^k terms each, top-M): the first
-    layers from the identity, batched (one graph launch per layer) against
-    the same 64 propagations run one after another as plain runs."""
+def measure_batch(args, layers, cap_log2, check_instances=8, autotune=True):
+    """64 independent open chains (the field-sweep recipe: n ~ U{16..64},
+    h ~ U[0.5, 2], seed 14400; J = 1, dtau = 0.02, delta = 1e-7, at most
+    2^cap_log2 terms each, top-M), batched (one graph launch per layer)
+    against the same 64 propagations run one after another as plain runs.
+    Returns the record (with the clocks sampled during both timings)."""
     import torch
     import paper_2601_14400_gb300 as itpp
-    if not os.path.exists(itpp.LIB_PATH):
-        itpp.build()
     ns, hs = wl.batch_field_sweep()
     hams = [wl.tfim_1d(n, 1.0, h) for n, h in zip(ns, hs)]
-    dtau, delta, M, L = 0.02, 1e-7, 1 << args.batch_cap_log2, args.batch_layers
+    dtau, delta, M, L = 0.02, 1e-7, 1 << cap_log2, layers
     stream = torch.cuda.Stream()
-    # batched
+    clocks = ClockSampler(torch.cuda.current_device())
     bp = itpp.BatchPropagator(hams, dtau, delta, M, cap_policy=1, stream=stream)
-    # launch shapes and table load from the autotuner, timed on these layers
-    tune = bp.autotune(probe_layers=L)
+    tune = bp.autotune(probe_layers=2) if autotune else None
     torch.cuda.synchronize()
+    clocks.start()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e0.record(stream)
     bp.apply_trotter_layer(L)
@@ -294,10 +308,11 @@ def run_batch(args):
     t_batch = e0.elapsed_time(e1)
     terms_b = sum(bp.stats(b)["terms_in"] for b in range(len(hams)))
     counts_b, _ = bp.counts()
-    energy_b = [bp.expect(b, wl.energy_observable(H)) for b, H in enumerate(hams[:4])]
+    chk = list(range(0, len(hams), max(1, len(hams) // check_instances)))[:check_instances]
+    terms_keep = {b: bp.terms(b) for b in chk}
+    cap_events = sum(bp.stats(b)["cap_events"] for b in range(len(hams)))
     bp.close()
-    # plain, one instance after another
-    t_plain, terms_p, counts_p, energy_p = 0.0, 0, [], []
+    t_plain, terms_p, counts_p, same_terms = 0.0, 0, [], True
     for b, H in enumerate(hams):
         g = itpp.Propagator(H.n, H.gate_x, H.gate_z, H.alpha, dtau, delta, M, 1, stream=stream)
         g.synchronize()
@@ -308,20 +323,34 @@ def run_batch(args):
         t_plain += e0.elapsed_time(e1)
         terms_p += g.stats()["terms_in"]
         counts_p.append(g.count())
-        if b < 4:
-            energy_p.append(g.expect(wl.energy_observable(H)))
+        if b in terms_keep:
+            px, pz, pc = g.sorted_terms()
+            bx, bz, bc = terms_keep[b]
+            order = np.lexsort(tuple(bz[:, w] for w in range(bz.shape[1] - 1, -1, -1)) +
+                               tuple(bx[:, w] for w in range(bx.shape[1] - 1, -1, -1)))
+            same_terms &= (np.array_equal(px, bx[order]) and np.array_equal(pz, bz[order]) and
+                           np.array_equal(pc.view(np.uint64), bc[order].view(np.uint64)))
         g.close()
-    same = (list(map(int, counts_b)) == counts_p) and energy_b == energy_p
-    line = {"metric": "batched vs plain: Pauli terms/s per Trotter gate", "mode": "batch",
+    clk = clocks.stop()
+    same = (list(map(int, counts_b)) == counts_p) and bool(same_terms)
+    return {"metric": "batched vs plain: Pauli terms/s per Trotter gate",
             "value": terms_b / (t_batch * 1e-3), "unit": UNIT,
             "plain_value": terms_p / (t_plain * 1e-3), "speedup": t_plain / t_batch,
             "batched_ms": t_batch, "plain_ms": t_plain, "identical_results": bool(same),
-            "autotune": tune,
+            "instances_compared_bitwise": len(chk), "cap_events": int(cap_events),
+            "autotune": tune, "clocks": clk,
             "config": {"workload": "field sweep: 64 open TFIM chains, n~U{16..64}, "
-                                   "h~U[0.5,2], J=1", "dtau": dtau, "delta": delta,
-                       "cap_M": M, "cap_policy": "top-M", "layers": L,
-                       "terms_final": int(sum(counts_b))},
-            "dtype": "f64", "data": "synthetic"}
+                                   "h~U[0.5,2], J=1 (seed 14400)", "dtau": dtau,
+                       "delta": delta, "cap_M": M, "cap_policy": "top-M", "layers": L,
+                       "terms_final": int(sum(counts_b))}}
+
+
+def run_batch(args):
+    import paper_2601_14400_gb300 as itpp
+    if not os.path.exists(itpp.LIB_PATH):
+        itpp.build()
+    line = measure_batch(args, args.batch_layers, args.batch_cap_log2)
+    line.update({"mode": "batch", "dtype": "f64", "data": "synthetic"})
     print(json.dumps(line), flush=True)
     return 0
 
@@ -447,21 +476,22 @@ def run_variants(args):
     return 0
 
 
-def run_adjoint(args):
+def measure_adjoint(args, layers, ckpt, fd=True):
     """n = 32 open chain with per-site fields and couplings (63 parameters),
-    dtau = 0.02, 50 layers, |c| <= 1e-7 dropped: the energy and <Z15 Z16>
-    gradients by the adjoint sweep (frozen support, snapshots every 10
-    layers), timed against the plain forward of the same propagation."""
+    dtau = 0.02, |c| <= 1e-7 dropped, at most 2^20 terms (top-M): the energy
+    and <Z15 Z16> gradients by the adjoint sweep (frozen support, snapshots
+    every ckpt layers), timed against the plain forward of the same
+    propagation; peak device memory sampled during the sweeps."""
     import torch
     import paper_2601_14400_gb300 as itpp
-    if not os.path.exists(itpp.LIB_PATH):
-        itpp.build()
     w = wl.WORKLOADS["adjoint_n32"]
     H = w.H
-    L = args.adjoint_layers
+    L = layers
     g = itpp.Propagator.from_workload(w)
     E = w.observables["energy"]
     ZZ = w.observables["Z15Z16"]
+    clocks = ClockSampler(torch.cuda.current_device())
+    clocks.start()
     free0 = torch.cuda.mem_get_info()[0]
     # plain forward
     g.reset()
@@ -472,7 +502,6 @@ def run_adjoint(args):
     t_fwd = time.perf_counter() - t0
     count = g.count()
     st = g.stats()
-    # adjoint (its own forward, snapshots, recomputation, reverse sweep)
     peak = [0]
     stop = [False]
 
@@ -482,47 +511,227 @@ def run_adjoint(args):
             time.sleep(0.02)
     th = threading.Thread(target=poll, daemon=True)
     th.start()
-    ck = args.adjoint_ckpt
     t0 = time.perf_counter()
-    fE, gE = g.adjoint(L, E, ckpt_every=ck)
+    fE, gE = g.adjoint(L, E, ckpt_every=ckpt)
     t_adjE = time.perf_counter() - t0
     t0 = time.perf_counter()
-    fZ, gZ = g.adjoint(L, ZZ, ckpt_every=ck)
+    fZ, gZ = g.adjoint(L, ZZ, ckpt_every=ckpt)
     t_adjZ = time.perf_counter() - t0
     stop[0] = True
     th.join()
+    clk = clocks.stop()
     # d<H>/dp: explicit term c_k plus the adjoint, d alpha_k / dp = -1
     dE = -(c_fwd + gE)
     dZ = -gZ
-    # loose check against central differences of the (unfrozen) forward
-    eps = 1e-5
-    fd = {}
-    for k in (0, H.n_gates - 1):
-        vals = []
-        for sgn in (1, -1):
-            a = H.alpha.copy()
-            a[k] += sgn * eps
-            g.set_alpha(a)
-            g.reset()
-            g.apply_trotter_layer(L)
-            vals.append(float(np.dot(a, g.coeffs(H.gate_x, H.gate_z))))
-        fd[k] = -(vals[0] - vals[1]) / (2 * eps)
-    g.set_alpha(H.alpha)
-    line = {"metric": "adjoint vs plain forward: wall-time ratio", "mode": "adjoint",
-            "value": t_adjE / t_fwd, "unit": "x forward", "forward_s": t_fwd,
-            "adjoint_energy_s": t_adjE, "adjoint_zz_s": t_adjZ,
-            "peak_device_bytes_approx": int(peak[0]), "terms_final": count,
-            "terms_in_forward": st["terms_in"],
-            "energy": fE, "zz_15_16": fZ,
-            "dE_dJ0": float(dE[0]), "dE_dh31": float(dE[-1]),
-            "fd_dE_dJ0": fd[0], "fd_dE_dh31": fd[H.n_gates - 1],
-            "grad_norm_energy": float(np.linalg.norm(dE)),
-            "grad_norm_zz": float(np.linalg.norm(dZ)),
-            "config": {"workload": w.name, "layers": L, "ckpt_every": ck,
-                       "delta": w.delta, "dtau": w.dtau, "params": H.n_gates},
+    rec = {"metric": "adjoint vs plain forward: wall-time ratio",
+           "value": t_adjE / t_fwd, "unit": "x forward", "forward_s": t_fwd,
+           "adjoint_energy_s": t_adjE, "adjoint_zz_s": t_adjZ,
+           "peak_device_bytes_approx": int(peak[0]), "terms_final": count,
+           "terms_in_forward": st["terms_in"], "energy": fE, "zz_15_16": fZ,
+           "dE_dJ0": float(dE[0]), "dE_dh31": float(dE[-1]),
+           "grad_norm_energy": float(np.linalg.norm(dE)),
+           "grad_norm_zz": float(np.linalg.norm(dZ)), "clocks": clk,
+           "config": {"workload": w.name, "layers": L, "ckpt_every": ckpt,
+                      "delta": w.delta, "dtau": w.dtau, "params": H.n_gates,
+                      "cap_M": w.cap_M, "cap_policy": "top-M"}}
+    if fd:
+        # loose check against central differences of the (unfrozen) forward
+        eps = 1e-5
+        fdv = {}
+        for k in (0, H.n_gates - 1):
+            vals = []
+            for sgn in (1, -1):
+                a = H.alpha.copy()
+                a[k] += sgn * eps
+                g.set_alpha(a)
+                g.reset()
+                g.apply_trotter_layer(L)
+                vals.append(float(np.dot(a, g.coeffs(H.gate_x, H.gate_z))))
+            fdv[k] = -(vals[0] - vals[1]) / (2 * eps)
+        g.set_alpha(H.alpha)
+        rec.update({"fd_dE_dJ0": fdv[0], "fd_dE_dh31": fdv[H.n_gates - 1]})
+    g.close()
+    return rec
+
+
+def run_adjoint(args):
+    import paper_2601_14400_gb300 as itpp
+    if not os.path.exists(itpp.LIB_PATH):
+        itpp.build()
+    line = measure_adjoint(args, args.adjoint_layers, args.adjoint_ckpt)
+    line.update({"mode": "adjoint", "dtype": "f64", "data": "synthetic"})
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def free_fermion_energy(J, h, beta):
+    """Exact thermal energy of the open chain H = -sum J_i Z_i Z_{i+1} -
+    sum h_i X_i: a Jordan-Wigner map makes it a free Majorana form whose
+    mode energies are twice the singular values s_k of the bidiagonal matrix
+    with h_i on the diagonal and J_i above it; <H>_beta = -sum s_k tanh(beta s_k)."""
+    h = np.asarray(h, dtype=float)
+    n = h.shape[0]
+    J = np.broadcast_to(np.asarray(J, dtype=float), (n - 1,))
+    s = np.linalg.svd(np.diag(h) + np.diag(J, 1), compute_uv=False)
+    return float(-np.sum(s * np.tanh(beta * s)))
+
+
+def run_kscan(args):
+    """K-truncation scan (Sec. III.B, fixed-K truncation): for open TFIM
+    chains (J = 1, h = 0.5) of N = 12..48 sites in steps of 4 and
+    beta in {0.08, 0.24, 0.8}, dtau = 0.02 (beta / dtau layers), no
+    coefficient threshold (delta = 0) and at most K terms (top-M), the
+    smallest K = 2^k, k = 9, 10, ..., 24, whose energy lies within
+    eps0 = 1e-2 (relative) of the exact free-fermion thermal energy.  A point
+    stops at the first K that reaches eps0, at K = 2^24, or when the scan's
+    time budget is spent (stated in the line)."""
+    import torch
+    import paper_2601_14400_gb300 as itpp
+    if not os.path.exists(itpp.LIB_PATH):
+        itpp.build()
+    eps0, dtau, J, h = 1e-2, 0.02, 1.0, 0.5
+    betas = [float(v) for v in args.kscan_betas.split(",")]
+    Ns = list(range(12, 49, 4))
+    stream = torch.cuda.Stream()
+    clocks = ClockSampler(torch.cuda.current_device())
+    clocks.start()
+    t_start = time.perf_counter()
+    table = []
+    out_of_budget = False
+    for beta in betas:
+        L = int(round(beta / dtau))
+        for N in Ns:
+            H = wl.tfim_1d(N, J, h)
+            E_ex = free_fermion_energy(J, [h] * N, L * dtau)
+            Eobs = wl.energy_observable(H)
+            row = {"beta": beta, "N": N, "layers": L, "E_exact": E_ex, "tried": []}
+            for k in range(9, 25):
+                if time.perf_counter() - t_start > args.kscan_budget:
+                    out_of_budget = True
+                    break
+                K = 1 << k
+                g = itpp.Propagator(H.n, H.gate_x, H.gate_z, H.alpha, dtau, 0.0, K, 1,
+                                    stream=stream)
+                e0 = torch.cuda.Event(enable_timing=True)
+                e1 = torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                g.apply_trotter_layer(L)
+                e1.record(stream)
+                E = g.expect(Eobs)
+                ms = e0.elapsed_time(e1)
+                terms = g.count()
+                g.close()
+                rel = abs(E - E_ex) / abs(E_ex)
+                row["tried"].append({"K": K, "rel_err": rel, "terms": terms, "ms": round(ms, 2)})
+                if rel <= eps0:
+                    row["K_min"] = K
+                    break
+            table.append(row)
+            if out_of_budget:
+                break
+        if out_of_budget:
+            break
+    clk = clocks.stop()
+    line = {"metric": "K-truncation scan: smallest K with relative energy error <= eps0",
+            "mode": "kscan", "eps0": eps0, "table": table,
+            "budget_s": args.kscan_budget, "out_of_budget": out_of_budget,
+            "wall_s": time.perf_counter() - t_start, "clocks": clk,
+            "config": {"workload": "open TFIM chains, J=1, h=0.5, N=12..48 step 4",
+                       "betas": betas, "dtau": dtau, "delta": 0.0, "K": "2^9 .. 2^24",
+                       "reference": "exact free-fermion thermal energy"},
             "dtype": "f64", "data": "synthetic"}
     print(json.dumps(line), flush=True)
     return 0
+
+
+def measure_layers_by_beta(g, stream, w, marks, start_layer):
+    """Continue the headline propagation layer by layer to the workload's last
+    layer (beta = n_layers * dtau), timing with events the layers at the
+    given marks (per-layer ms, N_in, re-partitions and full selects per gate)."""
+    import torch
+    clocks = ClockSampler(torch.cuda.current_device())
+    clocks.start()
+    out = []
+    layer = start_layer
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    t_start = time.perf_counter()
+    while layer < w.n_layers:
+        timed = (layer + 1) in marks
+        if timed:
+            s0 = g.stats()
+            e0.record(stream)
+        g.apply_trotter_layer(1)
+        layer += 1
+        if timed:
+            e1.record(stream)
+            g.synchronize()
+            s1 = g.stats()
+            ms = e0.elapsed_time(e1)
+            gates = max(1, s1["gates_applied"] - s0["gates_applied"])
+            n_in = s1["terms_in"] - s0["terms_in"]
+            out.append({"layer": layer, "beta": round(layer * w.dtau, 4), "ms": round(ms, 3),
+                        "terms_in": int(n_in), "terms_per_s": n_in / (ms * 1e-3),
+                        "repartitions_per_gate": (s1["repartitions"] - s0["repartitions"]) / gates,
+                        "select_full_per_gate": (s1["select_full"] - s0["select_full"]) / gates,
+                        "long_partitions_per_gate":
+                            (s1["long_partitions"] - s0["long_partitions"]) / gates})
+    g.synchronize()
+    clk = clocks.stop()
+    ms = [r["ms"] for r in out]
+    return {"points": out, "clocks": clk, "wall_s": time.perf_counter() - t_start,
+            "max_over_min_ms": (max(ms) / min(ms)) if ms else None,
+            "config": {"workload": w.name, "layers_total": w.n_layers, "dtau": w.dtau,
+                       "marks": sorted(marks)}}
+
+
+def measure_cfg3(args, timed_layers=2, max_setup=6):
+    """The 11x11 open lattice (n = 121, two mask words, 40 B per term), J = 1,
+    h = 3.04, dtau = 0.02, |c| <= 1e-5 dropped, at most 2^28 terms (top-M):
+    grown to the bound untimed, then timed_layers Trotter layers (341 gates
+    each) timed with CUDA events on the library stream."""
+    import torch
+    import paper_2601_14400_gb300 as itpp
+    w = wl.WORKLOADS["tfim2d_11x11"]
+    peak, peak_kind = load_peaks()
+    stream = torch.cuda.Stream()
+    g = itpp.Propagator.from_workload(w, stream=stream)
+    setup = 0
+    while setup < max_setup and g.count() < w.cap_M:
+        g.apply_trotter_layer(1)
+        setup += 1
+    g.synchronize()
+    clocks = ClockSampler(torch.cuda.current_device())
+    clocks.start()
+    s0 = g.stats()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    g.apply_trotter_layer(timed_layers)
+    e1.record(stream)
+    g.synchronize()
+    clk = clocks.stop()
+    ms = e0.elapsed_time(e1)
+    s1 = g.stats()
+    gates = max(1, s1["gates_applied"] - s0["gates_applied"])
+    n_in = s1["terms_in"] - s0["terms_in"]
+    n_out = s1["terms_out"] - s0["terms_out"]
+    tb = 16 * w.H.W + 8
+    b_alg = (n_in + n_out) * tb / gates
+    gate_ms = ms / gates
+    rec = {"metric": METRIC, "value": n_in / (ms * 1e-3), "unit": UNIT, "gate_ms": gate_ms,
+           "gate_roofline": {"achieved": b_alg / (gate_ms * 1e-3) / 1e9, "peak": peak,
+                             "unit": "GB/s", "frac": b_alg / (gate_ms * 1e-3) / 1e9 / peak,
+                             "peak_source": peak_kind, "alg_bytes_per_gate": b_alg},
+           "terms_at_start": s0["count"], "setup_layers": setup, "clocks": clk,
+           "repartitions_per_gate": (s1["repartitions"] - s0["repartitions"]) / gates,
+           "select_full_per_gate": (s1["select_full"] - s0["select_full"]) / gates,
+           "config": {"workload": w.name, "n": w.H.n, "mask_words": w.H.W, "dtau": w.dtau,
+                      "delta": w.delta, "cap_M": w.cap_M, "cap_policy": "top-M",
+                      "timed_layers": timed_layers,
+                      "bound_note": "the threshold alone passes 2^29 terms by the third "
+                                    "layer, so the run keeps at most 2^28 (top-M)"}}
+    g.close()
+    torch.cuda.synchronize()
+    return rec
 
 
 def main():
@@ -535,6 +744,8 @@ def main():
         return run_synth(args)
     if args.mode == "variants":
         return run_variants(args)
+    if args.mode == "kscan":
+        return run_kscan(args)
     w = wl.WORKLOADS[args.workload]
     if args.cap_log2:
         w.cap_M = 1 << args.cap_log2
@@ -665,7 +876,32 @@ def main():
         t, dt, ng = oracle_sample(w, args.ref_gates)
         cpu = {"value": t / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
                "sample": f"{w.name}: first {ng} gates from the identity, single thread "
-                         f"({t} term-gates in {dt:.1f} s)"}
+                         f"({t} term-gates in {dt:.1f} s)",
+               "config": {"workload": w.name, "gates": ng, "from": "the identity",
+                          "mean_terms_per_gate": t / max(ng, 1),
+                          "note": "the GPU line is timed at the 2^26 bound; the oracle "
+                                  "cannot hold that state in reasonable time, so this is "
+                                  "the same workload's first gates (small states)"}}
+
+    # the rest of the headline run (beta up to 2), then the other workloads of
+    # the metric: the 2D lattice, adjoint and batched runs against plain ones
+    extras = {}
+    if rank == 0 and not args.no_extras:
+        marks = {int(v) for v in args.beta_marks.split(",") if v}
+        extras["layers_by_beta"] = measure_layers_by_beta(
+            g, stream, w, marks, setup + args.warmup + args.steps)
+    g.close()
+    torch.cuda.synchronize()
+    if rank == 0 and not args.no_extras:
+        for key, fn in (("cfg3", lambda: measure_cfg3(args, args.cfg3_layers)),
+                        ("adjoint_vs_plain", lambda: measure_adjoint(args, 50, 10, fd=False)),
+                        ("batch_vs_plain", lambda: measure_batch(
+                            args, args.extra_batch_layers, args.extra_batch_cap_log2))):
+            try:
+                extras[key] = fn()
+            except Exception as e:   # reported, never hidden
+                extras[key] = {"error": f"{type(e).__name__}: {e}"}
+            torch.cuda.synchronize()
 
     if rank == 0:
         line = {
@@ -705,11 +941,13 @@ def main():
             "table_probes_per_term": (st1["table_probes"] - st0["table_probes"]) / max(terms_in, 1),
             "repartitions_per_gate": (st1["repartitions"] - st0["repartitions"]) / max(gates, 1),
             "select_candidates_per_gate": (st1["select_candidates"] - st0["select_candidates"]) / max(gates, 1),
+            "select_full_per_gate": (st1["select_full"] - st0["select_full"]) / max(gates, 1),
+            "long_partitions_per_gate": (st1["long_partitions"] - st0["long_partitions"]) / max(gates, 1),
             "select_range_bits": int(st1["select_range"]).bit_length(),
             "terms_in_timed": int(terms_in),
         }
+        line.update(extras)
         print(json.dumps(line), flush=True)
-    g.close()
     if world > 1:
         import torch.distributed as dist
         dist.destroy_process_group()

@@ -129,11 +129,20 @@ typedef struct {
     uint64_t table_probes;    /* merge-table slots visited (build + lookups)    */
     uint64_t kernel_launches; /* kernels this handle has launched (host count)  */
     uint64_t repartitions;    /* partitioned merge: scatters run (window starts,
-                               * state changes, partitions past the split limit) */
-    uint64_t select_candidates; /* top-M selects: terms in the threshold's first
-                                 * digit, summed over gates                      */
-    uint64_t select_range;    /* last top-M select: largest |c| pattern minus the
-                               * threshold's pattern (the first digit's range)   */
+                               * state changes, gates partitioned by pair key)   */
+    uint64_t select_candidates; /* top-M selects: terms listed around the
+                                 * threshold, summed over gates                  */
+    uint64_t select_range;    /* last top-M select: width of the |c| pattern range
+                               * its candidates were listed from                 */
+    uint64_t select_full;     /* top-M selects that passed over every stored
+                               * coefficient (the threshold lay outside the range
+                               * the merge listed, or no range was known yet)    */
+    uint64_t long_partitions; /* partitioned merge: partitions above one CTA's
+                               * staging capacity, merged in sub-passes          */
+    uint64_t error_site;      /* where the first device error was raised (a code
+                               * of the library's kernels; 0 while status is ok),
+                               * reported together with the status by
+                               * itpp_get_stats even when the status is an error */
 } itpp_stats;
 
 /* ---------------------------------------------------------------------------
@@ -427,9 +436,10 @@ itpp_status itpp_batch_expect(itpp_batch_handle h, int b, const uint64_t* obs_x,
  *   alpha, dtau        Q's coefficient and the step: theta = alpha * dtau.
  *   delta              threshold (>= 0).
  *   d_keys_in          device, n_in terms, each 2W words: x[0..W-1] then
- *                      z[0..W-1]; distinct strings, the identity present.
- *   d_coef_in          device, n_in normalised coefficients (the identity's
- *                      is taken as exactly one).
+ *                      z[0..W-1]; distinct strings, the identity present
+ *                      (an input without it is reported through d_n_out).
+ *   d_coef_in          device, n_in finite normalised coefficients (the
+ *                      identity's is taken as exactly one).
  *   n_in               1 .. ITPP_NOALLOC_MAX_TERMS(W); larger is
  *                      ITPP_ERR_CAPACITY.
  *   d_keys_out/_coef_out  device, room for out_capacity >= 2 * n_in terms
@@ -437,13 +447,20 @@ itpp_status itpp_batch_expect(itpp_batch_handle h, int b, const uint64_t* obs_x,
  *                      in an unspecified order, normalised.
  *   d_n_out            device, receives the kept count, or UINT64_MAX when a
  *                      device-side error (merge-table probe limit, identity
- *                      truncated) occurred.
+ *                      truncated or absent from the input) occurred.
  *   d_trace_out        device or NULL: the identity coefficient before the
  *                      rescaling.
  *   cuda_stream        stream to run on.
  * Asynchronous.  The first call on a device looks up the scratch's device
  * address (cudaGetSymbolAddress) with that device current; make that first
- * call before any stream capture.  All calls share the scratch: calls whose
+ * call before any stream capture.  Under CUDA's lazy module loading (the
+ * default), that first call may also be what loads this library's module on
+ * the device and sets the scratch aside, which allocates device memory and
+ * can synchronise: a caller that must not allocate makes one warm-up call
+ * (or creates any handle of this library) on each device before entering its
+ * allocation-free region.  All calls share the scratch and it keeps the last
+ * call's contents (each call takes a fresh generation of the merge table, and
+ * the table is cleared once when the 32-bit generation wraps): calls whose
  * work overlaps on the GPU race and corrupt each other; serialise them. */
 itpp_status itpp_gate_apply_noalloc(int n, const uint64_t* gate_x, const uint64_t* gate_z,
                                     double alpha, double dtau, double delta,

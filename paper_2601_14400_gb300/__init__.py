@@ -44,7 +44,8 @@ class itpp_stats(ctypes.Structure):
                 ("cap_events", ctypes.c_uint64), ("count", ctypes.c_uint64),
                 ("table_probes", ctypes.c_uint64), ("kernel_launches", ctypes.c_uint64),
                 ("repartitions", ctypes.c_uint64), ("select_candidates", ctypes.c_uint64),
-                ("select_range", ctypes.c_uint64)]
+                ("select_range", ctypes.c_uint64), ("select_full", ctypes.c_uint64),
+                ("long_partitions", ctypes.c_uint64), ("error_site", ctypes.c_uint64)]
 
 
 class ItppError(RuntimeError):
@@ -325,10 +326,16 @@ class Propagator:
         _check(lib().itpp_coeffs(self._h, pox, poz, m, out.ctypes.data_as(_f64p)), "itpp_coeffs")
         return out
 
-    def stats(self):
+    def stats(self, check=True):
+        """Device counters; with check=False the counters are returned even
+        when the handle holds an error (then "status" names it)."""
         s = itpp_stats()
-        _check(lib().itpp_get_stats(self._h, ctypes.byref(s)), "itpp_get_stats")
-        return {k: int(getattr(s, k)) for k, _ in itpp_stats._fields_}
+        st = lib().itpp_get_stats(self._h, ctypes.byref(s))
+        if check:
+            _check(st, "itpp_get_stats")
+        d = {k: int(getattr(s, k)) for k, _ in itpp_stats._fields_}
+        d["status"] = int(st)
+        return d
 
     def reset(self):
         _check(lib().itpp_reset(self._h), "itpp_reset")

@@ -621,6 +621,10 @@ extern "C" itpp_status itpp_set_alpha(itpp_handle h, const double* alpha) {
     if (!h || !alpha) return ITPP_ERR_ARG;
     for (int k = 0; k < h->user_gates; ++k)
         if (!std::isfinite(alpha[k])) return ITPP_ERR_ARG;
+    for (size_t k = 0; k < h->gates.size(); ++k) {   // cosh / sinh overflow
+        const double theta = (alpha[h->src_gate[k]] * h->src_scale[k]) * h->dtau;
+        if (!std::isfinite(std::cosh(theta)) || !std::isfinite(std::sinh(theta))) return ITPP_ERR_ARG;
+    }
     cudaStreamSynchronize(h->stream);
     for (size_t k = 0; k < h->gates.size(); ++k) {
         HostGate& g = h->gates[k];

@@ -202,8 +202,12 @@ __global__ void k_import_begin(DevCtl* ctl, uint64_t count) {
         ctl->stat_cands = 0;
         ctl->stat_range = 0;
         ctl->stat_peak = count;
+        ctl->stat_sel_full = ctl->stat_long = 0;
         ctl->sel_k = 0;   // reused below as "identity seen" flag
         ctl->pend = 0;
+        ctl->seg = 0;
+        ctl->sp_lo = ctl->sp_hi = 0;
+        ctl->sp_shift = 0;
     }
 }
 
@@ -334,10 +338,14 @@ __global__ void k_reset_identity(BufsA<W> B, DevCtl* ctl) {
         ctl->sel_tie_n = 0;
         ctl->sel_k = 0;
         ctl->pend = 0;
+        ctl->seg = 0;
+        ctl->sp_lo = ctl->sp_hi = 0;
+        ctl->sp_shift = 0;
         ctl->stat_gates = ctl->stat_in = ctl->stat_out = ctl->stat_cap = ctl->stat_probes = 0;
         ctl->stat_scatters = 0;
         ctl->stat_cands = 0;
         ctl->stat_range = 0;
+        ctl->stat_sel_full = ctl->stat_long = 0;
         ctl->stat_peak = 1;
     }
 }

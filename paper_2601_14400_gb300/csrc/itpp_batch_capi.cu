@@ -200,6 +200,9 @@ itpp_status itpp_batch_create(int B, const int* n, const int* n_gates, const uin
         for (int b = 0; b < B; ++b)
             for (int j = 0; j < n_gates[b]; ++j, ++k) {
                 if (!std::isfinite(alpha[k])) return ITPP_ERR_ARG;
+                if (!std::isfinite(std::cosh(alpha[k] * dtau)) ||
+                    !std::isfinite(std::sinh(alpha[k] * dtau)))
+                    return ITPP_ERR_ARG;   // the gate's weights overflow
                 if (!bits_ok(n[b], W, gate_x + k * W) || !bits_ok(n[b], W, gate_z + k * W))
                     return ITPP_ERR_ARG;
             }
@@ -399,6 +402,9 @@ itpp_status itpp_batch_get_stats(itpp_batch_handle h, int b, itpp_stats* o) {
     o->repartitions = 0;
     o->select_candidates = 0;
     o->select_range = 0;
+    o->select_full = 0;
+    o->long_partitions = 0;
+    o->error_site = c->status ? c->err_info : 0;
     o->kernel_launches = h->launches;
     return (itpp_status)c->status;
 }

@@ -57,12 +57,15 @@ void free_all(itpp_ctx* h) {
     if (h->s.part_keys) cudaFree(h->s.part_keys);
     if (h->s.part_coef) cudaFree(h->s.part_coef);
     if (h->s.part_cursor) cudaFree(h->s.part_cursor);
-    for (int i = 0; i < 2; ++i)
+    for (int i = 0; i < 2; ++i) {
         if (h->s.part_desc[i]) cudaFree(h->s.part_desc[i]);
+        if (h->s.chunks[i]) cudaFree(h->s.chunks[i]);
+    }
     if (h->s.ctl) cudaFree(h->s.ctl);
     if (h->obs_mem) cudaFree(h->obs_mem);
     if (h->sort_mem) cudaFree(h->sort_mem);
     if (h->psd_mem) cudaFree(h->psd_mem);
+    if (h->s.cand.cnt) cudaFree(h->s.cand.cnt);
     if (h->h_ctl) cudaFreeHost(h->h_ctl);
     for (int k = 0; k < kKinds; ++k)
         for (auto& e : h->ev[k]) { cudaEventDestroy(e.a); cudaEventDestroy(e.b); }
@@ -328,12 +331,25 @@ itpp_status itpp_create(int n, const uint64_t* gate_x, const uint64_t* gate_z,
     s.num_sms = sms;
     s.cap_M = p->cap_M;
     s.buf_cap = 2 * p->cap_M;
+    s.max_ctas = std::min(8 * sms, 1024);   // the select reads at most 1024 candidate regions
+    if (p->merge_path == 0) {
+        // merge CTAs claim output chunks: room for what the chunks leave
+        // unused, and an even count (the L2 bulk prefetch rounds byte ranges
+        // to 16 bytes); candidate positions are 32-bit
+        s.chunk = merge_chunk(p->cap_M, s.max_ctas);
+        s.buf_cap += merge_slack(p->cap_M, s.max_ctas);
+        s.buf_cap += s.buf_cap & 1ULL;
+        if (s.buf_cap >= (1ULL << 32)) {
+            delete h;
+            return ITPP_ERR_ARG;
+        }
+    }
     s.cap_policy = p->cap_policy;
     s.delta = p->delta + 0.0;   // -0 becomes +0 (the threshold compares bit patterns)
     s.load_pct = p->table_load_pct ? p->table_load_pct : 50;
     // defaults: 512 x 2 for the partitioned merge (a whole partition in
     // registers), 256 x 2 for the global-table merge
-    s.block = p->block_threads ? p->block_threads : (p->merge_path == 0 ? 512 : 256);
+    s.block = p->block_threads ? p->block_threads : 256;
     s.ipt = p->items_per_thread ? p->items_per_thread : 2;
     s.merge_deferred = p->merge_path == 0;
     s.probe_limit = 4096;
@@ -370,6 +386,10 @@ itpp_status itpp_create(int n, const uint64_t* gate_x, const uint64_t* gate_z,
         g.chd = std::cosh(theta);
         g.qyy = yy & 3;
         g.maxw = p->max_weight ? p->max_weight : (1 << 30);
+        if (!std::isfinite(g.ch) || !std::isfinite(g.msh)) {   // |alpha dtau| beyond ~710
+            delete h;
+            return ITPP_ERR_ARG;
+        }
     }
 
     bool ok = true;
@@ -383,7 +403,7 @@ itpp_status itpp_create(int n, const uint64_t* gate_x, const uint64_t* gate_z,
     if (ok && p->merge_path == 0) {
         // the scatter buffer: partitions of a fixed stride, 2.5x the mean
         // partition at the bound (a window group adds up to 4^sites terms)
-        s.part_cap = 2 * p->cap_M + p->cap_M / 2 + (1ULL << 18);
+        s.part_cap = 2 * p->cap_M + p->cap_M / 2 + (1ULL << 18);   // even
         s.part_target = p->partition_target ? p->partition_target : partition_target_default(W);
         s.part_max = partition_max(p->cap_M, s.part_target);
         ok &= cudaMalloc(&s.part_keys, s.part_cap * 16 * W) == cudaSuccess;
@@ -393,6 +413,27 @@ itpp_status itpp_create(int n, const uint64_t* gate_x, const uint64_t* gate_z,
         for (int i = 0; i < 2; ++i)
             ok &= ok && cudaMalloc(reinterpret_cast<void**>(&s.part_desc[i]),
                                    (size_t)s.part_max * sizeof(PartDesc)) == cudaSuccess;
+        // output chunks: every claim takes at least one chunk of the buffer,
+        // and each CTA leaves one partly used
+        s.max_chunks = (uint32_t)(s.buf_cap / s.chunk + 2ULL * (uint64_t)s.max_ctas + 64);
+        for (int i = 0; i < 2; ++i)
+            ok &= ok && cudaMalloc(reinterpret_cast<void**>(&s.chunks[i]),
+                                   (size_t)s.max_chunks * sizeof(ChunkDesc)) == cudaSuccess;
+        // the merge's candidate regions for the top-M select: about half the
+        // bound's worth of entries over the merge's CTAs
+        uint64_t region = p->cap_M / (2ULL * (uint64_t)s.max_ctas);
+        if (region < 64) region = 64;
+        const uint64_t ent = region * (uint64_t)s.max_ctas;
+        const size_t cnt_bytes = ((size_t)s.max_ctas * 4 + 255) / 256 * 256;
+        void* cm = nullptr;
+        ok &= ok && cudaMalloc(&cm, cnt_bytes + (size_t)ent * 12) == cudaSuccess;
+        if (cm) {
+            s.cand.cnt = static_cast<uint32_t*>(cm);
+            s.cand.v = reinterpret_cast<unsigned long long*>(static_cast<char*>(cm) + cnt_bytes);
+            s.cand.idx = reinterpret_cast<uint32_t*>(s.cand.v + ent);
+            s.cand.region = region;
+        }
+        s.cand_hi = std::max<uint64_t>(4096, std::min<uint64_t>(p->cap_M / 16, ent / 8));
         plan_windows(W, h->gates);
     }
     if (ok && p->merge_path == 1) {
@@ -487,6 +528,9 @@ itpp_status itpp_get_stats(itpp_handle h, itpp_stats* o) {
     o->repartitions = c.stat_scatters;
     o->select_candidates = c.stat_cands;
     o->select_range = c.stat_range;
+    o->select_full = c.stat_sel_full;
+    o->long_partitions = c.stat_long;
+    o->error_site = c.status ? c.err_info : 0;
     o->kernel_launches = h->launches;
     return st;
 }
@@ -591,6 +635,8 @@ itpp_status itpp_load(itpp_handle h, const char* path) {
 itpp_status itpp_set_terms(itpp_handle h, const uint64_t* x, const uint64_t* z, const double* c,
                            uint64_t count) {
     if (!h || !x || !z || !c || count < 1 || count > h->s.cap_M) return ITPP_ERR_ARG;
+    for (uint64_t i = 0; i < count; ++i)
+        if (!std::isfinite(c[i])) return ITPP_ERR_ARG;   // a NaN or inf coefficient
     if (h->sticky == ITPP_ERR_CUDA) return h->sticky;
     cudaStreamSynchronize(h->stream);
     // stage the planes in buffer 1, import into buffer 0

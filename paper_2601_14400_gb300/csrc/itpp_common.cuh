@@ -101,8 +101,30 @@ struct DevCtl {
     // partitioned merge: where the next merge finds its partitions
     unsigned int part_P;             // partitions of the current state
     int part_from_scatter;           // 1: in the scatter buffer; 0: segments of the state
-    int part_over;                   // this gate left a partition above the split limit
+    int part_over;                   // this gate's partitions hold for this gate only
     int need_scatter;                // ... so the next gate re-partitions
+    // segmented state: the merge writes every partition's children as one
+    // segment of a chunk its CTA claimed (alloc[] is the chunk allocator of
+    // each buffer); the buffer then holds seg_P segments, described by the
+    // partition descriptors, with unused room between them
+    int seg;                         // 1: the current buffer is segmented
+    unsigned int seg_P;
+    unsigned long long alloc[2];
+    unsigned int nchunk[2];          // output chunks in use per buffer (contiguous runs)
+    // top-M select folded into the merge: the merge counts its kept
+    // children above sp_hi and lists those in [sp_lo, sp_hi] (a range around
+    // the previous gate's threshold); the select then reads only that list
+    unsigned long long sp_lo, sp_hi; // candidate range (sp_hi == 0: none)
+    unsigned long long sp_above;     // kept children with pattern > sp_hi
+    int sp_ovf;                      // a CTA's candidate region overflowed
+    int sp_shift;                    // log2 of the range's half-width (0: unset)
+    unsigned int cand_regions;       // regions of the candidate list in use
+    int sel_fast;                    // this select reads the merge's candidates
+    int sp_reason;                   // why not: 1 no range, 2 list too long, 3 threshold
+                                     // above the range, 4 below it
+    int sel_top;                     // bits of v = pattern - sel_lo still to resolve
+    unsigned long long sel_lo;       // offset of the select's values
+    unsigned long long stat_sel_full, stat_long;
     // top-M select geometry: largest |c| pattern the gate wrote (partitioned
     // merge), the value the select uses, and the last-CTA counter
     unsigned long long out_max;

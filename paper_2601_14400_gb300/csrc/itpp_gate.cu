@@ -226,56 +226,81 @@ __device__ __forceinline__ PKey<W> pend_tie_key(const DevCtl* ctl) {
     return tk;
 }
 
-// Materialise a deferred select: compact the kept terms into the other
-// buffer (normaliser unchanged) and switch to it.
+// Materialise the state of the partitioned merge for a reader that wants a
+// contiguous run: apply a deferred select (its kept set), and gather the
+// segments of a segmented buffer, into the other buffer (normaliser
+// unchanged), then switch to it.
+__device__ __forceinline__ bool mat_needed(const DevCtl* ctl) { return ctl->pend || ctl->seg; }
+
 __global__ void k_mat_begin(DevCtl* ctl) {
-    if (threadIdx.x != 0 || !ctl->pend || ctl->status) return;
+    if (threadIdx.x != 0 || !mat_needed(ctl) || ctl->status) return;
     const int cur = ctl->cur;
     ctl->count[cur ^ 1] = 0ULL;
     ctl->norm[cur ^ 1] = ctl->norm[cur];
     ctl->rnorm[cur ^ 1] = ctl->rnorm[cur];
 }
 
+// One round of up to BLOCK terms [i0, i0 + BLOCK) of a run of n (every
+// thread calls it).
+template <int W, int BLOCK>
+__device__ __forceinline__ void mat_round(const Bufs<W>& B, DevCtl* ctl, int cur, uint64_t off,
+                                          uint64_t n, uint64_t i0, bool pend, unsigned long long T,
+                                          bool all_ties, const PKey<W>& tk, uint32_t* s_scan,
+                                          unsigned long long* s_base) {
+    const uint64_t i = i0 + threadIdx.x;
+    PKey<W> K;
+    double c = 0;
+    bool keep = false;
+    if (i < n) {
+        K = load_key_stream(B.key(cur) + off + i);
+        c = __ldcs(B.coef(cur) + off + i);
+        keep = !pend || cap_keep(K, c, T, all_ties, tk);
+        if (key_is_zero(K) && !keep) set_status(ctl, ST_TRACE_ZERO, 3);
+    }
+    uint32_t tot;
+    const uint32_t o = block_exclusive_scan<BLOCK>(keep ? 1u : 0u, &tot, s_scan);
+    if (threadIdx.x == 0)
+        *s_base = tot ? atomicAdd(&ctl->count[cur ^ 1], (unsigned long long)tot) : 0ULL;
+    __syncthreads();
+    if (keep) {
+        store_key_stream(B.key(cur ^ 1) + *s_base + o, K);
+        __stcs(B.coef(cur ^ 1) + *s_base + o, c);
+    }
+}
+
 template <int W, int BLOCK>
 __global__ void __launch_bounds__(BLOCK)
-k_materialize(Bufs<W> B, DevCtl* ctl) {
-    if (!ctl->pend || ctl->status) return;
+k_materialize(Bufs<W> B, DevCtl* ctl, const ChunkDesc* chunks0, const ChunkDesc* chunks1) {
+    if (!mat_needed(ctl) || ctl->status) return;
     __shared__ uint32_t s_scan[BLOCK / 32];
     __shared__ unsigned long long s_base;
     const int cur = ctl->cur;
-    uint64_t n = ctl->pend_n;
-    if (n > ctl->buf_cap) n = ctl->buf_cap;
+    const bool pend = ctl->pend != 0;
     const unsigned long long T = ctl->pend_T;
     const bool all_ties = ctl->pend_all_ties;
     const PKey<W> tk = pend_tie_key<W>(ctl);
-    const uint64_t tiles = (n + BLOCK - 1) / BLOCK;
-    for (uint64_t t = blockIdx.x; t < tiles; t += gridDim.x) {
-        const uint64_t i = t * BLOCK + threadIdx.x;
-        PKey<W> K;
-        double c = 0;
-        bool keep = false;
-        if (i < n) {
-            K = load_key_stream(B.key(cur) + i);
-            c = __ldcs(B.coef(cur) + i);
-            keep = cap_keep(K, c, T, all_ties, tk);
-            if (key_is_zero(K) && !keep) set_status(ctl, ST_TRACE_ZERO, 3);
+    if (ctl->seg) {
+        const ChunkDesc* din = cur ? chunks1 : chunks0;
+        const uint32_t P = ctl->nchunk[cur];
+        for (uint32_t p = blockIdx.x; p < P; p += gridDim.x) {
+            const uint64_t off = din[p].off, n = din[p].cnt;
+            for (uint64_t i0 = 0; i0 < n; i0 += BLOCK)
+                mat_round<W, BLOCK>(B, ctl, cur, off, n, i0, pend, T, all_ties, tk, s_scan, &s_base);
         }
-        uint32_t tot;
-        const uint32_t off = block_exclusive_scan<BLOCK>(keep ? 1u : 0u, &tot, s_scan);
-        if (threadIdx.x == 0)
-            s_base = tot ? atomicAdd(&ctl->count[cur ^ 1], (unsigned long long)tot) : 0ULL;
-        __syncthreads();
-        if (keep) {
-            store_key_stream(B.key(cur ^ 1) + s_base + off, K);
-            __stcs(B.coef(cur ^ 1) + s_base + off, c);
-        }
+    } else {
+        uint64_t n = pend ? ctl->pend_n : ctl->count[cur];
+        if (n > ctl->buf_cap) n = ctl->buf_cap;
+        const uint64_t tiles = (n + BLOCK - 1) / BLOCK;
+        for (uint64_t t = blockIdx.x; t < tiles; t += gridDim.x)
+            mat_round<W, BLOCK>(B, ctl, cur, 0, n, t * BLOCK, pend, T, all_ties, tk, s_scan, &s_base);
     }
 }
 
 __global__ void k_mat_end(DevCtl* ctl) {
-    if (threadIdx.x != 0 || !ctl->pend) return;
+    if (threadIdx.x != 0 || !mat_needed(ctl)) return;
     if (!ctl->status) ctl->cur ^= 1;
     ctl->pend = 0;
+    ctl->seg = 0;
 }
 
 // ---------------------------------------------------------------------------
@@ -377,13 +402,14 @@ cudaError_t launch_cap_select(const DeviceState& s, cudaStream_t st) {
 }
 
 int cap_launches(const DeviceState& s) {
-    return s.merge_deferred ? 3 : 5 * 2 + 1 + 8 * s.W * 2 + 3;
+    return s.merge_deferred ? select_deferred_launches(s.W) : 5 * 2 + 1 + 8 * s.W * 2 + 3;
 }
 
 template <int W>
 static cudaError_t materialize_w(const DeviceState& s, cudaStream_t st) {
     k_mat_begin<<<1, 32, 0, st>>>(s.ctl);
-    k_materialize<W, 256><<<stream_grid(s, 256, 8), 256, 0, st>>>(bufs_of<W>(s), s.ctl);
+    k_materialize<W, 256><<<stream_grid(s, 256, 8), 256, 0, st>>>(bufs_of<W>(s), s.ctl,
+                                                                  s.chunks[0], s.chunks[1]);
     k_mat_end<<<1, 32, 0, st>>>(s.ctl);
     return cudaGetLastError();
 }

@@ -255,10 +255,16 @@ __device__ __forceinline__ int post_one(DevCtl* ctl, uint64_t cap_M, int cap_pol
     ctl->pend = 0;   // a deferred select was applied by this gate's scatter or merge
     ctl->need_scatter = ctl->part_over;
     ctl->part_over = 0;
+    // a child beyond the largest double (or NaN) from finite inputs: the
+    // weights overflowed the state's range; the largest written pattern
+    // (partitioned merge) and the normaliser (every path) show it
+    constexpr unsigned long long kInfBits = 0x7ff0000000000000ULL;
+    if (ctl->out_max >= kInfBits) set_status(ctl, ST_STATE, 4);
     ctl->sel_hi = ctl->out_max;
     ctl->out_max = 0;
     const int cur = ctl->cur, nxt = cur ^ 1;
     const unsigned long long n_in = ctl->count[cur], n_out = ctl->count[nxt];
+    if (abs_pattern(ctl->norm[nxt]) >= kInfBits) set_status(ctl, ST_STATE, 5);
     ctl->cur = nxt;
     ctl->rnorm[nxt] = __ddiv_rn(1.0, ctl->norm[nxt]);
     ctl->gen = ctl->gen + 1u;

@@ -17,6 +17,26 @@ struct PartDesc {
     unsigned int pad;
 };
 
+// One output chunk of a partitioned merge: a contiguous run of stored terms
+// (the partitions' segments the CTA packed into it), for readers that walk
+// the whole state rather than its partitions.
+struct ChunkDesc {
+    unsigned long long off;   // first term in the state buffer
+    unsigned int cnt;         // terms stored
+    unsigned int pad;
+};
+
+// The candidate list the partitioned merge fills for the top-M select: CTA r
+// of the merge owns entries [r * region, (r + 1) * region) of v (the
+// candidate's |c| pattern minus the range's low end) and idx (its position
+// in the output buffer), and writes how many it used to cnt[r].
+struct CandRegions {
+    unsigned long long* v = nullptr;
+    uint32_t* idx = nullptr;
+    uint32_t* cnt = nullptr;
+    uint64_t region = 0;
+};
+
 // Device resources of one propagation (or of one batch instance table).
 struct DeviceState {
     int n = 0, W = 1;
@@ -39,6 +59,12 @@ struct DeviceState {
     uint64_t part_cap = 0;
     uint32_t part_max = 0;
     int part_target = 0;              // mean partition size of the scatter
+    uint64_t chunk = 0;               // output chunk a merge CTA claims at a time (terms)
+    ChunkDesc* chunks[2] = {nullptr, nullptr};   // [max_chunks] per state buffer
+    uint32_t max_chunks = 0;
+    int max_ctas = 0;                 // CTAs of the merge and select grids at most
+    CandRegions cand;                 // one allocation: cnt[max_ctas], then v, then idx
+    uint64_t cand_hi = 0;             // candidate count above which the range narrows
     // top-M select leaves its kept set as a predicate for the next scatter
     bool merge_deferred = false;
 };
@@ -61,16 +87,20 @@ struct HostGate {
 cudaError_t launch_gate_insert(const DeviceState& s, const HostGate& g, cudaStream_t st);
 cudaError_t launch_gate_main(const DeviceState& s, const HostGate& g, cudaStream_t st);
 cudaError_t launch_gate_post(const DeviceState& s, cudaStream_t st);
-// Partitioned merge: scatter by pair key, then one shared-memory table per
-// partition (the default merge of a single propagation).
-// force = 1 re-partitions unconditionally (first gate of a window, or the
-// state changed outside the window); force = 0 only when the previous gate
-// left a partition above the split limit.
+// Partitioned merge: scatter by the window's masked key (or the pair key),
+// then one shared-memory table per partition (the default merge of a single
+// propagation).  force = 1 re-partitions unconditionally (first gate of a
+// window, or the state changed outside the window); force = 0 only when the
+// previous gate's partitions held for that gate alone (pair-key mode).
 cudaError_t launch_part_scatter(const DeviceState& s, const HostGate& g, int force,
                                 cudaStream_t st);
 cudaError_t launch_part_merge(const DeviceState& s, const HostGate& g, cudaStream_t st);
 uint32_t partition_max(uint64_t cap_M, int target);
 int partition_target_default(int W);
+// Output chunk of the partitioned merge for a term bound, and the room the
+// chunks may leave unused in a state buffer (added to its capacity).
+uint64_t merge_chunk(uint64_t cap_M, int max_ctas);
+uint64_t merge_slack(uint64_t cap_M, int max_ctas);
 // Group consecutive gates into windows of at most a few sites (sets the
 // window fields of every gate).
 void plan_windows(int W, std::vector<HostGate>& gates);
@@ -83,7 +113,9 @@ cudaError_t launch_cap_select(const DeviceState& s, cudaStream_t st);
 // The top-M select of the partitioned merge (itpp_select.cu): leaves the
 // kept set as a predicate for the next gate's reads.
 cudaError_t launch_select_deferred(const DeviceState& s, cudaStream_t st);
-// Apply a deferred top-M select (compaction); a no-op when none is pending.
+int select_deferred_launches(int W);
+// Apply a deferred top-M select and gather a segmented state into one
+// contiguous run (compaction); a no-op when neither is there.
 cudaError_t launch_materialize(const DeviceState& s, cudaStream_t st);
 // Sort-based merge path (children buffer, radix sort, segmented reduce).
 cudaError_t launch_gate_sorted(const DeviceState& s, const HostGate& g, void* scratch,

@@ -10,12 +10,17 @@
 // GPU that loads this library holds until the process exits.
 //
 // The scratch is shared by every call on a device and keeps the last call's
-// contents.  The merge table needs no clearing: each call takes a new
-// generation number and slots tagged with an older one count as free (the
-// array starts zeroed and generations start at one).  The counters that must
-// start at zero are reset by the call's first kernel.  Two calls whose work
-// overlaps on the GPU (different streams, or different host threads) race on
-// this scratch and corrupt each other's results; serialise them.
+// contents.  The merge table needs no clearing between calls: each call takes
+// a new generation number and slots tagged with an older one count as free
+// (the array starts zeroed and generations start at one); when the 32-bit
+// generation wraps, the call's first kernel zeroes the whole table once.  The
+// counters that must start at zero are reset by that kernel too.  Two calls
+// whose work overlaps on the GPU (different streams, or different host
+// threads) race on this scratch and corrupt each other's results; serialise
+// them.  With CUDA's lazy module loading, the first call on a device may be
+// the one that loads this library's module and sets the array aside (which
+// allocates and can synchronise): callers that must not allocate make one
+// call, or create any handle of this library, on that device beforehand.
 #include <cmath>
 #include <cstdint>
 #include <cstring>
@@ -59,29 +64,49 @@ itpp_status scratch_address(void** out) {
     return ITPP_OK;
 }
 
+// The normaliser's value before the gate's merge writes it: a NaN pattern
+// that no merge produces, so a call whose input lacks the identity (and
+// which therefore never writes it) is told apart.
+constexpr unsigned long long kNoIdentity = 0x7ff80000deadbeefULL;
+
 // Reset the control block for a call: input in buffer 0 with n_in terms,
-// output in buffer 1, a fresh table generation.
-__global__ void k_noalloc_begin(uint64_t n_in, uint64_t buf_cap) {
-    if (threadIdx.x != 0) return;
+// output in buffer 1, a fresh table generation.  When the generation counter
+// wraps, every slot is cleared (tag 0 = free) before generation 1 is used,
+// so a slot last written about 2^32 calls earlier cannot pass for a live one.
+__global__ void __launch_bounds__(256) k_noalloc_begin(uint64_t n_in, uint64_t buf_cap) {
+    __shared__ int s_wrap;
     DevCtl* ctl = reinterpret_cast<DevCtl*>(g_noalloc_scratch);
-    ctl->status = 0;
-    ctl->err_info = 0;
-    ctl->cur = 0;
-    ctl->count[0] = n_in;
-    ctl->count[1] = 0;
-    ctl->buf_cap = buf_cap;
-    ctl->norm[0] = 1.0;
-    ctl->rnorm[0] = 1.0;
-    ctl->norm[1] = 1.0;
-    ctl->rnorm[1] = 1.0;
-    ctl->gen = ctl->gen + 1u;
-    if (ctl->gen == 0u) ctl->gen = 1u;
+    if (threadIdx.x == 0) {
+        ctl->status = 0;
+        ctl->err_info = 0;
+        ctl->cur = 0;
+        ctl->count[0] = n_in;
+        ctl->count[1] = 0;
+        ctl->buf_cap = buf_cap;
+        ctl->norm[0] = 1.0;
+        ctl->rnorm[0] = 1.0;
+        ctl->norm[1] = __longlong_as_double((long long)kNoIdentity);
+        ctl->rnorm[1] = 1.0;
+        const unsigned int g = ctl->gen + 1u;
+        s_wrap = g == 0u;
+        ctl->gen = g ? g : 1u;
+    }
+    __syncthreads();
+    if (s_wrap) {
+        uint4* t = reinterpret_cast<uint4*>(g_noalloc_scratch + kCtlBytes);
+        for (size_t i = threadIdx.x; i < kTableBytes / sizeof(uint4); i += blockDim.x)
+            t[i] = make_uint4(0u, 0u, 0u, 0u);
+    }
 }
 
-// Count and trace of the output; an error leaves count = UINT64_MAX.
+// Count and trace of the output; an error (or an input without the
+// identity) leaves count = UINT64_MAX and trace = NaN.
 __global__ void k_noalloc_end(uint64_t* d_n_out, double* d_trace_out) {
     if (threadIdx.x != 0) return;
     DevCtl* ctl = reinterpret_cast<DevCtl*>(g_noalloc_scratch);
+    if (!ctl->status &&
+        (unsigned long long)__double_as_longlong(ctl->norm[1]) == kNoIdentity)
+        itpp::set_status(ctl, itpp::ST_TRACE_ZERO, 50);
     if (ctl->status) {
         *d_n_out = ~0ULL;
         if (d_trace_out) *d_trace_out = __longlong_as_double(0x7ff8000000000000LL);
@@ -172,7 +197,7 @@ extern "C" itpp_status itpp_gate_apply_noalloc(
     g.msh = -std::sinh(theta);
     g.qyy = yy & 3;
 
-    k_noalloc_begin<<<1, 32, 0, stream>>>(n_in, s.buf_cap);
+    k_noalloc_begin<<<1, 256, 0, stream>>>(n_in, s.buf_cap);
     if (itpp::launch_gate_insert(s, g, stream) != cudaSuccess) return ITPP_ERR_CUDA;
     if (itpp::launch_gate_main(s, g, stream) != cudaSuccess) return ITPP_ERR_CUDA;
     k_noalloc_end<<<1, 32, 0, stream>>>(d_n_out, d_trace_out);

@@ -11,13 +11,22 @@
 // at a time per CTA: the partition's terms stay in registers, the commuting
 // ones publish (key, child for the partner) in a shared-memory table, every
 // term merges with its partner's child, and the kept children of the
-// partition are written as one contiguous segment of the next state buffer
-// (one atomic per partition).  The segments are the partitions of the next
-// gate of the window, so no scatter runs between the gates of a window.  A
-// group holds at most 4^|S| terms; a partition whose output outgrows the
-// shared table's limit makes the next gate re-partition.  A gate acting on
-// more sites than a window allows is a window of its own, partitioned by its
-// pair key (the member of {K, QK} with the gate's lowest bit clear).
+// partition are written as one contiguous segment of an output chunk that
+// the CTA claimed beforehand (a global atomic every few hundred partitions,
+// none per partition).  The segments, listed by the partition descriptors,
+// are the partitions of the next gate of the window, so no scatter runs
+// between the gates of a window.  A group holds at most 4^|S| terms; a
+// partition that outgrows the register chunk is merged in sub-passes, each
+// taking the pairs of one hash class of the key with the gate's sites
+// cleared, so no partition size forces a re-partition.  A gate acting on more
+// sites than a window allows is a window of its own, partitioned by its pair
+// key (the member of {K, QK} with the gate's lowest bit clear).
+//
+// The top-M select (Sec. II.C, term bound) is folded into the merge: every
+// kept child is compared with a range around the previous gate's threshold;
+// the merge counts the children above it and lists those inside it, and the
+// select (itpp_select.cu) then works on that short list instead of passing
+// over every coefficient.
 #include "itpp_common.cuh"
 #include "itpp_gate_body.cuh"
 #include "itpp_launch.h"
@@ -27,22 +36,16 @@ namespace itpp {
 namespace {
 
 
-// Shared-table geometry per word count: slots, the mean partition size the
-// scatter aims for, the largest partition output a following gate of the
-// window may read (its commuting terms stay under 70% of the slots), and the
-// largest window (sites; a group holds at most 4^sites terms).
+// Partition geometry per word count: the mean partition size the scatter
+// aims for, and the largest window (sites; a group holds at most 4^sites
+// terms).
 template <int W> struct PartGeom;
 template <> struct PartGeom<1> {
-    static constexpr int kSlots = 2048, kTarget = 700, kSplit = 1400, kWinSites = 5;
+    static constexpr int kTarget = 700, kWinSites = 5;
 };
 template <> struct PartGeom<2> {
-    static constexpr int kSlots = 1024, kTarget = 300, kSplit = 700, kWinSites = 4;
+    static constexpr int kTarget = 300, kWinSites = 4;
 };
-
-template <int W>
-constexpr size_t part_smem_bytes() {
-    return (size_t)PartGeom<W>::kSlots * (sizeof(PKey<W>) + sizeof(double) + sizeof(uint32_t));
-}
 
 struct PartPlan {
     uint32_t P;     // partitions
@@ -123,55 +126,127 @@ __device__ __forceinline__ Pending<W> pending_of(const DevCtl* ctl) {
     return q;
 }
 
+// Prefetch [p, p + bytes) into L2 with one bulk (TMA) request; the range is
+// widened to 16-byte boundaries, which every buffer it is used on allows
+// (its byte size is a multiple of 16).
+__device__ __forceinline__ void l2_prefetch_bulk(const void* p, uint64_t bytes) {
+    const uint64_t a = reinterpret_cast<uint64_t>(p);
+    const uint64_t lo = a & ~15ULL;
+    uint64_t sz = ((a + bytes + 15ULL) & ~15ULL) - lo;
+    if (sz > (1ULL << 20)) sz = 1ULL << 20;
+    if (sz) asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" :: "l"(lo), "r"((uint32_t)sz)
+                         : "memory");
+}
+
+// ---------------------------------------------------------------------------
+// Bulk (TMA) copies into shared memory, completed on an mbarrier.  A copy
+// needs 16-byte aligned addresses and a size that is a multiple of 16 bytes.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ uint32_t smem_addr(const void* p) {
+    return (uint32_t)__cvta_generic_to_shared(p);
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" :: "r"(smem_addr(bar)), "r"(count)
+                 : "memory");
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+
+// Arrive on the barrier and announce `bytes` of copies that complete it.
+__device__ __forceinline__ void mbar_expect(uint64_t* bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;"
+                 :: "r"(smem_addr(bar)), "r"(bytes) : "memory");
+}
+
+__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t bytes,
+                                         uint64_t* bar) {
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes "
+                 "[%0], [%1], %2, [%3];"
+                 :: "r"(smem_addr(dst)), "l"(src), "r"(bytes), "r"(smem_addr(bar)) : "memory");
+}
+
+// Generic-proxy accesses to shared memory made before this fence are ordered
+// before later bulk copies into it.
+__device__ __forceinline__ void fence_async_shared() {
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+
+// Wait for the barrier's phase `parity` to complete, at most `limit` polls
+// (each poll may itself suspend the thread for a while).  False: timed out.
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, uint32_t limit) {
+    const uint32_t a = smem_addr(bar);
+    for (uint32_t it = 0; it < limit; ++it) {
+        uint32_t done;
+        // the thread sleeps in the wait until the phase completes or the
+        // hint (nanoseconds) runs out, instead of polling
+        asm volatile("{\n\t.reg .pred p;\n\t"
+                     "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n\t"
+                     "selp.u32 %0, 1, 0, p;\n\t}"
+                     : "=r"(done) : "r"(a), "r"(parity), "r"(1000000u) : "memory");
+        if (done) return true;
+    }
+    return false;
+}
+
+// Sub-pass of a long partition's commuting string: a hash of the key with
+// the gate's sites cleared, which K and Q.K share (they differ exactly on
+// Q's bits), so a string and its partner always fall into the same one.
+template <int W>
+__device__ __forceinline__ uint32_t sub_pass(const PKey<W>& K, const GateArg<W>& g, uint32_t k) {
+    PKey<W> m;
+#pragma unroll
+    for (int w = 0; w < W; ++w) { m.x[w] = K.x[w] & ~g.qx[w]; m.z[w] = K.z[w] & ~g.qz[w]; }
+    return (uint32_t)((key_hash(m) * (uint64_t)k) >> 32);
+}
+
+// Append one value per lane that has one (every lane of the warp calls it)
+// to this CTA's region of the candidate list: one shared-memory atomic per
+// warp; entries past the region's end are dropped and counted, and the
+// select then falls back to its full passes.
+__device__ __forceinline__ void cand_push(bool hit, unsigned long long v, uint64_t pos,
+                                          const CandRegions& cd, uint32_t* s_cn) {
+    const unsigned int m = __ballot_sync(0xffffffffu, hit);
+    if (!m) return;
+    const int lane = threadIdx.x & 31, leader = __ffs(m) - 1;
+    uint32_t q = 0;
+    if (lane == leader) q = atomicAdd(s_cn, (uint32_t)__popc(m));
+    q = __shfl_sync(0xffffffffu, q, leader);
+    if (hit) {
+        const uint64_t r = (uint64_t)q + __popc(m & ((1u << lane) - 1u));
+        if (r < cd.region) {
+            const uint64_t e = (uint64_t)blockIdx.x * cd.region + r;
+            cd.v[e] = v;
+            cd.idx[e] = (uint32_t)pos;
+        }
+    }
+}
+
 }  // namespace
 
 // Scatter the current state into the partitions of a window (force), or,
-// inside a window, only when the previous gate left a partition above the
-// split limit; otherwise the next merge reads the previous merge's segments.
+// inside a window, only when the previous gate's partitions hold for that
+// gate alone; otherwise the next merge reads the previous merge's segments.
+// The state is a contiguous run of terms, or (after a partitioned merge)
+// the segments its descriptors list.
 template <int W>
-__global__ void __launch_bounds__(256)
-k_part_scatter(Bufs<W> B, DevCtl* ctl, PKey<W>* pk, double* pc, unsigned int* cursor,
-               uint64_t pbuf_cap, uint32_t p_max, GateArg<W> g, PartFn<W> f, int force,
-               int n_sites, int target) {
-    if (ctl->status) return;
-    const int cur = ctl->cur;
-    if (!force && !ctl->need_scatter) {
-        if (blockIdx.x == 0 && threadIdx.x == 0) {
-            ctl->count[cur ^ 1] = 0ULL;
-            ctl->part_from_scatter = 0;
-        }
-        return;
-    }
-    const uint64_t n = live_count(ctl, cur);
-    const PartPlan pl = part_plan(n, pbuf_cap, p_max, target);
-    const bool fallback = !f.pair && !window_fits(n_sites, f.sites, n);
-    if (fallback) f.pair = 1;
-    if (blockIdx.x == 0 && threadIdx.x == 0) {
-        ctl->count[cur ^ 1] = 0ULL;
-        ctl->part_from_scatter = 1;
-        ctl->part_P = pl.P;
-        ctl->stat_scatters += 1;
-        if (fallback) ctl->part_over = 1;   // the partitions hold for this gate only
-    }
-    const PKey<W>* __restrict__ kin = B.key(cur);
-    const double* __restrict__ cin = B.coef(cur);
-    // a deferred top-M select: scan every stored term, keep its kept set
-    const Pending<W> pd = pending_of<W>(ctl);
-    uint64_t n_scan = n;
-    if (pd.on) n_scan = ctl->pend_n < ctl->buf_cap ? ctl->pend_n : ctl->buf_cap;
+__device__ __forceinline__ void scatter_run(const PKey<W>* __restrict__ kin,
+                                            const double* __restrict__ cin, uint64_t n,
+                                            uint64_t first, uint64_t stride, const Pending<W>& pd,
+                                            DevCtl* ctl, PKey<W>* pk, double* pc,
+                                            unsigned int* cursor, const PartPlan& pl,
+                                            const GateArg<W>& g, const PartFn<W>& f) {
     // whole warps iterate together (the cursor claim below is warp-wide);
     // U items per thread per round, their loads issued before any claim
     constexpr int U = 4;
-    const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
     const unsigned int lt = (1u << (threadIdx.x & 31)) - 1u;
-    for (uint64_t i0 = (uint64_t)blockIdx.x * blockDim.x; i0 < n_scan; i0 += U * stride) {
+    for (uint64_t i0 = first; i0 < n; i0 += U * stride) {
         PKey<W> K[U];
         double c[U];
         bool live[U];
 #pragma unroll
         for (int u = 0; u < U; ++u) {
             const uint64_t i = i0 + (uint64_t)u * stride + threadIdx.x;
-            live[u] = i < n_scan;
+            live[u] = i < n;
             c[u] = 0.0;
 #pragma unroll
             for (int w = 0; w < W; ++w) { K[u].x[w] = 0; K[u].z[w] = 0; }
@@ -208,54 +283,87 @@ k_part_scatter(Bufs<W> B, DevCtl* ctl, PKey<W>* pk, double* pc, unsigned int* cu
     }
 }
 
-// Per-item quantities of the gate on one stored term (Eq. for the commuting
-// branch: cosh(theta) P and -sinh(theta) s QP).  c is the normalised input
-// coefficient, b = c * (-sinh(theta) s) the child it sends to its partner QP.
-// For a commuting pair {K, QK} the product sign s is the same seen from both
-// members (Q K = s QK implies Q QK = s K), so the partner's incoming addend
-// is exactly the b its own thread computes: each term multiplies once by
-// rnorm, once by ch and once by msh, and adds its partner's b.
 template <int W>
-struct PartItem {
-    PKey<W> K;
-    double c, b;
-    bool comm, live;
-};
-
-template <int W>
-__device__ __forceinline__ PartItem<W> part_item(const PKey<W>* kp, const double* cp, uint64_t i,
-                                                 uint64_t np, const GateArg<W>& g, double rnorm,
-                                                 const Pending<W>& pd, DevCtl* ctl) {
-    PartItem<W> it;
-    double raw = 0.0;
-    bool neg = false;
-#pragma unroll
-    for (int w = 0; w < W; ++w) { it.K.x[w] = 0; it.K.z[w] = 0; }
-    it.live = false;
-    it.comm = false;
-    if (i < np) {
-        it.K = load_key_stream(kp + i);
-        raw = __ldcs(cp + i);
-        // a deferred top-M select drops the terms outside its kept set here
-        it.live = !pd.on || cap_keep(it.K, raw, pd.T, pd.all_ties, pd.tk);
-        if (!it.live && key_is_zero(it.K)) set_status(ctl, ST_TRACE_ZERO, 43);
-        it.comm = it.live && commutes(it.K, g);
-        neg = it.comm && product_negative(it.K, g);
+__global__ void __launch_bounds__(256, W == 1 ? 6 : 4)
+k_part_scatter(Bufs<W> B, DevCtl* ctl, PKey<W>* pk, double* pc, unsigned int* cursor,
+               uint64_t pbuf_cap, uint32_t p_max, GateArg<W> g, PartFn<W> f, int force,
+               int n_sites, int target, const ChunkDesc* chunks0, const ChunkDesc* chunks1) {
+    if (ctl->status) return;
+    const int cur = ctl->cur;
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        // the next merge's counters
+        ctl->count[cur ^ 1] = 0ULL;
+        ctl->alloc[cur ^ 1] = 0ULL;
+        ctl->nchunk[cur ^ 1] = 0u;
+        ctl->sp_above = 0ULL;
+        ctl->sp_ovf = 0;
     }
-    // the same double-precision operations on every lane; the identity's
-    // normalised value is exactly 1
-    it.c = key_is_zero(it.K) ? 1.0 : __dmul_rn(raw, rnorm);
-    const double m = __longlong_as_double(
-        __double_as_longlong(g.msh) ^ (neg ? (long long)0x8000000000000000ULL : 0LL));
-    it.b = __dmul_rn(it.c, m);
-    return it;
+    if (!force && !ctl->need_scatter) {
+        if (blockIdx.x == 0 && threadIdx.x == 0) ctl->part_from_scatter = 0;
+        return;
+    }
+    const uint64_t n = live_count(ctl, cur);
+    const PartPlan pl = part_plan(n, pbuf_cap, p_max, target);
+    const bool fallback = !f.pair && !window_fits(n_sites, f.sites, n);
+    if (fallback) f.pair = 1;
+    // the chunks of the previous merge's output
+    const bool seg = ctl->seg != 0;
+    const uint32_t n_chunks = ctl->nchunk[cur];
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        ctl->part_from_scatter = 1;
+        ctl->part_P = pl.P;
+        ctl->stat_scatters += 1;
+        if (fallback) ctl->part_over = 1;   // the partitions hold for this gate only
+    }
+    const Pending<W> pd = pending_of<W>(ctl);
+    // one loop for both layouts (a single copy of the scatter body): each
+    // output chunk of the previous merge by one CTA, or the contiguous run by
+    // the whole grid (with a deferred top-M select every stored term is
+    // scanned and its kept set applied)
+    const ChunkDesc* __restrict__ cin = cur ? chunks1 : chunks0;
+    uint64_t n_scan = n;
+    if (!seg && pd.on) n_scan = ctl->pend_n < ctl->buf_cap ? ctl->pend_n : ctl->buf_cap;
+    const uint32_t runs = seg ? n_chunks : 1u;
+    for (uint32_t s = seg ? blockIdx.x : 0u; s < runs; s += seg ? gridDim.x : 1u) {
+        const uint64_t off = seg ? cin[s].off : 0ULL;
+        const uint64_t cnt = seg ? (uint64_t)cin[s].cnt : n_scan;
+        const uint64_t first = seg ? 0ULL : (uint64_t)blockIdx.x * blockDim.x;
+        const uint64_t stride = seg ? (uint64_t)blockDim.x : (uint64_t)gridDim.x * blockDim.x;
+        scatter_run(B.key(cur) + off, B.coef(cur) + off, cnt, first, stride, pd, ctl, pk, pc,
+                    cursor, pl, g, f);
+    }
 }
 
-// Slot of a key in a partition's table (at most a few thousand slots): a
-// multiply-xor of the key's 32-bit halves and one xorshift-multiply round,
-// about a third of the instructions of the full key hash.  Partitions are
-// chosen by the full hash of a different key (masked or pair key), so the
-// two are independent.
+// Items a CTA stages in shared memory for one pass, and the slots of its
+// pair table (at most half full).
+template <int W> struct StageGeom;
+template <> struct StageGeom<1> { static constexpr int kItems = 1024, kSlots = 2048; };
+template <> struct StageGeom<2> { static constexpr int kItems = 512, kSlots = 1024; };
+
+// Dynamic shared memory of the merge: the staged keys, their values (raw
+// coefficient in, normalised coefficient after phase A, merged child after
+// phase B; two spare slots let a copy start at the 16-byte boundary below an
+// odd element), the partner children b, the pair table and per-item flags.
+template <int W>
+struct Stage {
+    static constexpr int C = StageGeom<W>::kItems, S = StageGeom<W>::kSlots;
+    static constexpr size_t kKeys = 0;
+    static constexpr size_t kVals = kKeys + sizeof(PKey<W>) * C;
+    static constexpr size_t kB = kVals + sizeof(double) * (C + 2);
+    static constexpr size_t kTab = kB + sizeof(double) * C;
+    static constexpr size_t kFlags = kTab + sizeof(uint32_t) * S;
+    static constexpr size_t kBytes = (kFlags + C + 15) / 16 * 16;
+    static_assert(kVals % 16 == 0 && kB % 16 == 0 && kTab % 16 == 0, "alignment");
+};
+
+// Waits on a staging copy's barrier before the CTA gives up: each wait
+// sleeps up to a millisecond, and a copy of a few tens of kilobytes completes
+// within microseconds; this bound is seconds.
+constexpr uint32_t kWaitPolls = 4096u;
+
+// Slot of a key in a CTA's pair table: a multiply-xor of the key's 32-bit
+// halves and one xorshift-multiply round.  Partitions are chosen by the full
+// hash of a different key (masked or pair key), so the two are independent.
 template <int W>
 __device__ __forceinline__ uint32_t slot_hash(const PKey<W>& k) {
     constexpr uint32_t C[8] = {0x9E3779B1u, 0x85EBCA77u, 0xC2B2AE3Du, 0x27D4EB2Fu,
@@ -272,20 +380,21 @@ __device__ __forceinline__ uint32_t slot_hash(const PKey<W>& k) {
     return h;
 }
 
-// Shared-memory table of one partition: commuting keys and their b.  A slot
-// belongs to the partition whose tag it holds; tags grow with the partition
-// index, so a slot still tagged by an earlier partition of this CTA is free
-// and the table needs no clearing between partitions.
+// Pair table of one pass: slot = (tag << 16) | index of a staged commuting
+// string.  Tags grow with every pass of the CTA, so a slot of an earlier
+// pass is free and the table needs no clearing.
 template <int W>
-__device__ __forceinline__ bool part_insert(const PartItem<W>& it, PKey<W>* t_keys, double* t_b,
-                                            uint32_t* t_tag, uint32_t tag) {
-    constexpr uint32_t S = PartGeom<W>::kSlots;
-    uint32_t h = slot_hash(it.K) & (S - 1);
+__device__ __forceinline__ bool pair_insert(const PKey<W>& K, uint32_t i, uint32_t* tab,
+                                            uint32_t tag) {
+    constexpr uint32_t S = StageGeom<W>::kSlots;
+    const uint32_t mine = (tag << 16) | i;
+    uint32_t h = slot_hash(K) & (S - 1);
     for (uint32_t q = 0; q < S; ++q) {
-        if (atomicMax(t_tag + h, tag) < tag) {
-            t_keys[h] = it.K;
-            t_b[h] = it.b;
-            return true;
+        uint32_t v = tab[h];
+        while ((v >> 16) != tag) {          // free: claim it
+            const uint32_t o = atomicCAS(tab + h, v, mine);
+            if (o == v) return true;
+            v = o;
         }
         h = (h + 1) & (S - 1);
     }
@@ -293,79 +402,28 @@ __device__ __forceinline__ bool part_insert(const PartItem<W>& it, PKey<W>* t_ke
 }
 
 template <int W>
-__device__ __forceinline__ bool part_find(const PKey<W>& P, const PKey<W>* t_keys,
-                                          const double* t_b, const uint32_t* t_tag, uint32_t tag,
+__device__ __forceinline__ bool pair_find(const PKey<W>& P, const PKey<W>* keys_s,
+                                          const double* b_s, const uint32_t* tab, uint32_t tag,
                                           double* out) {
-    constexpr uint32_t S = PartGeom<W>::kSlots;
+    constexpr uint32_t S = StageGeom<W>::kSlots;
     uint32_t h = slot_hash(P) & (S - 1);
     for (uint32_t q = 0; q < S; ++q) {
-        if (t_tag[h] != tag) return false;
-        if (key_eq(t_keys[h], P)) { *out = t_b[h]; return true; }
+        const uint32_t v = tab[h];
+        if ((v >> 16) != tag) return false;
+        const uint32_t j = v & 0xffffu;
+        if (key_eq(keys_s[j], P)) { *out = b_s[j]; return true; }
         h = (h + 1) & (S - 1);
     }
     return false;
 }
 
-// Branch, merge and truncation of one item against the complete table:
-// va (self child, merged) and whether the QP child is emitted.
-template <int W>
-__device__ __forceinline__ void part_children(const PartItem<W>& it, const GateArg<W>& g,
-                                              const PKey<W>* t_keys, const double* t_b,
-                                              const uint32_t* t_tag, uint32_t tag, double* va,
-                                              bool* emit_b) {
-    double pb = 0.0;
-    bool found = false;
-    if (it.comm) found = part_find(key_xor(it.K, g), t_keys, t_b, t_tag, tag, &pb);
-    const double a1 = __dmul_rn(it.c, g.ch);          // cosh(theta) P
-    const double sum = __dadd_rn(a1, pb);             // + the partner's child
-    *va = !it.comm ? it.c : (found ? sum : a1);       // {P,Q} = 0: unchanged
-    *emit_b = it.comm && !found;
-}
-
-// Flags of one item after the merge: bit 0 keeps the self child (merged
-// value va), bit 1 emits the QK child (value b).  The identity is always
-// kept and its merged value is the next normaliser.
-template <int W>
-__device__ __forceinline__ uint32_t part_flags(const PartItem<W>& it, const GateArg<W>& g,
-                                               const PKey<W>* t_keys, const double* t_b,
-                                               const uint32_t* t_tag, uint32_t tag,
-                                               unsigned long long dbits, DevCtl* ctl, int nxt,
-                                               double* va) {
-    bool eb;
-    part_children(it, g, t_keys, t_b, t_tag, tag, va, &eb);
-    if (!it.live) return 0u;
-    // threshold and weight cutoff on the merged children (Sec. II.B)
-    bool keep_a = above(*va, dbits) && light(it.K, g.maxw);
-    const bool keep_b = eb && above(it.b, dbits) && light(key_xor(it.K, g), g.maxw);
-    if (key_is_zero(it.K)) {
-        ctl->norm[nxt] = *va;
-        if (!keep_a) set_status(ctl, ST_TRACE_ZERO, 1);
-        keep_a = true;
-    }
-    return (keep_a ? 1u : 0u) | (keep_b ? 2u : 0u);
-}
-
-template <int W>
-__device__ __forceinline__ void part_write(const PartItem<W>& it, const GateArg<W>& g, double va,
-                                           uint32_t fl, PKey<W>* kout, double* cout,
-                                           uint64_t pos) {
-    if (fl & 1u) {
-        store_key_stream(kout + pos, it.K);
-        __stcs(cout + pos, va);
-        ++pos;
-    }
-    if (fl & 2u) {
-        store_key_stream(kout + pos, key_xor(it.K, g));
-        __stcs(cout + pos, it.b);
-    }
-}
-
-// Exclusive block scan with one barrier: every warp writes its total, and
-// after the barrier every thread sums the totals of the warps before its own
-// (s_warp may be rewritten only after the caller's next barrier).
+// Exclusive block scan with one barrier: every warp writes its total, then
+// every warp scans the warp totals with shuffles (s_warp may be rewritten
+// only after the caller's next barrier).
 template <int BLOCK>
-__device__ __forceinline__ uint32_t scan_one_barrier(uint32_t v, uint32_t* s_warp,
-                                                     uint32_t* total) {
+__device__ __forceinline__ uint32_t block_scan_1bar(uint32_t v, uint32_t* s_warp,
+                                                    uint32_t* total) {
+    constexpr int NW = BLOCK / 32;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     uint32_t x = v;
 #pragma unroll
@@ -375,49 +433,207 @@ __device__ __forceinline__ uint32_t scan_one_barrier(uint32_t v, uint32_t* s_war
     }
     if (lane == 31) s_warp[warp] = x;
     __syncthreads();
-    uint32_t before = 0, tot = 0;
+    uint32_t t = lane < NW ? s_warp[lane] : 0u;
 #pragma unroll
-    for (int w = 0; w < BLOCK / 32; ++w) {
-        const uint32_t t = s_warp[w];
-        before += w < warp ? t : 0u;
-        tot += t;
+    for (int o = 1; o < NW; o <<= 1) {
+        const uint32_t y = __shfl_up_sync(0xffffffffu, t, o);
+        if (lane >= o) t += y;
     }
-    *total = tot;
-    return before + x - v;
+    const uint32_t before = __shfl_sync(0xffffffffu, t, warp > 0 ? warp - 1 : 0);
+    *total = __shfl_sync(0xffffffffu, t, NW - 1);
+    return (warp > 0 ? before : 0u) + x - v;
 }
 
-// One partition at a time per CTA.  The partition comes from the scatter
-// buffer (fixed stride, cursor) or is a segment the previous gate of the
-// window wrote (descriptor).  Its items stay in registers (BLOCK x IPT of
-// them; a longer partition takes a two-pass path that reloads), the
-// commuting ones publish (key, b) in a shared-memory table, then every item
-// merges with its partner's b, and the kept children of the partition go to
-// one contiguous segment of the next state buffer, recorded as the
-// partition's descriptor for the next gate.  Three barriers per partition:
-// table built; warp totals written; segment claimed.  The table is read only
-// before the second, so the next partition's inserts (tagged p + 1, see
-// part_insert) may start as soon as a thread has passed the third.
-template <int W, int kPBlock, int kPIpt>
-__global__ void __launch_bounds__(kPBlock, (W == 1 ? 1536 : 1024) / kPBlock)
+// Statistics of the kept children for the top-M select: the largest
+// pattern, the count above the candidate range, the candidates inside it.
+struct SelStats {
+    const unsigned long long* range;   // shared: candidate range [lo, hi] (hi == 0: none)
+    unsigned long long out_max;
+    uint32_t above;
+};
+
+// Write one staged item's kept children at pos (and pos + 1) and fold them
+// into the statistics.  Every lane of the warp calls it.
+template <int W>
+__device__ __forceinline__ void stage_emit(const PKey<W>& K, double va, double b, uint32_t o,
+                                           const GateArg<W>& g, PKey<W>* kout, double* cout,
+                                           uint64_t pos, SelStats& st, const CandRegions& cd,
+                                           uint32_t* s_cn) {
+    if (o & 1u) {
+        store_key_stream(kout + pos, K);
+        __stcs(cout + pos, va);
+    }
+    const uint64_t pb = pos + (o & 1u);
+    if (o & 2u) {
+        store_key_stream(kout + pb, key_xor(K, g));
+        __stcs(cout + pb, b);
+    }
+    const unsigned long long a = (o & 1u) ? abs_pattern(va) : 0ULL;
+    const unsigned long long bb = (o & 2u) ? abs_pattern(b) : 0ULL;
+    st.out_max = max(st.out_max, max(a, bb));
+    const unsigned long long hi = st.range[1];
+    if (hi) {   // uniform
+        const unsigned long long lo = st.range[0], w = hi - lo;
+        st.above += (a > hi ? 1u : 0u) + (bb > hi ? 1u : 0u);
+        // a - lo <= w on unsigned values: lo <= a <= hi (a kept child has a > 0)
+        cand_push((o & 1u) && a - lo <= w, a - lo, pos, cd, s_cn);
+        cand_push((o & 2u) && bb - lo <= w, bb - lo, pb, cd, s_cn);
+    }
+}
+
+template <int W>
+struct PassArgs {
+    PKey<W>* keys_s;
+    double* vals_s;     // item i's value at vals_s[shift + i]
+    double* b_s;
+    uint32_t* tab;
+    uint8_t* flags_s;
+    uint32_t* s_warp;
+    uint32_t* s_cn;
+};
+
+// One pass of the gate over n staged strings: phase A (the deferred select's
+// kept set, commutation, sign, the normalised coefficient c and the partner
+// child b = c (-sinh(theta)) s, commuting strings into the pair table),
+// phase B (the partner's b, the merged child, threshold and weight cutoff,
+// the identity's merged coefficient as the next normaliser), a block scan of
+// the kept children, and the write pass from `base` on (room the caller
+// holds).  Three barriers; the staging arrays are free again when it
+// returns.  Returns the kept children written (the same on every thread).
+template <int W, int BLOCK>
+__device__ __forceinline__ uint32_t stage_pass(const PassArgs<W>& a, uint32_t n, uint32_t shift,
+                                               const GateArg<W>& g, const Pending<W>& pd,
+                                               double rnorm, unsigned long long dbits,
+                                               DevCtl* ctl, int nxt, uint32_t tag,
+                                               PKey<W>* kout, double* cout, SelStats& st,
+                                               const CandRegions& cd, unsigned long long base) {
+    double* vals = a.vals_s + shift;
+    // phase A
+    for (uint32_t i = threadIdx.x; i < n; i += BLOCK) {
+        const PKey<W> K = a.keys_s[i];
+        const double raw = vals[i];
+        const bool live = !pd.on || cap_keep(K, raw, pd.T, pd.all_ties, pd.tk);
+        const bool id = key_is_zero(K);
+        if (!live && id) set_status(ctl, ST_TRACE_ZERO, 43);
+        const bool comm = live && commutes(K, g);
+        const bool neg = comm && product_negative(K, g);
+        // the identity's normalised value is exactly 1
+        const double c = id ? 1.0 : __dmul_rn(raw, rnorm);
+        const double m = __longlong_as_double(
+            __double_as_longlong(g.msh) ^ (neg ? (long long)0x8000000000000000ULL : 0LL));
+        vals[i] = c;
+        a.b_s[i] = __dmul_rn(c, m);
+        a.flags_s[i] = (uint8_t)((live ? 1u : 0u) | (comm ? 2u : 0u));
+        if (comm && !pair_insert(K, i, a.tab, tag)) set_status(ctl, ST_CAPACITY, 41);
+    }
+    __syncthreads();                                                  // (1) table built
+    // phase B
+    uint32_t cnt = 0;
+    for (uint32_t i = threadIdx.x; i < n; i += BLOCK) {
+        const uint32_t f = a.flags_s[i];
+        uint32_t o = 0;
+        if (f & 1u) {
+            const PKey<W> K = a.keys_s[i];
+            const double c = vals[i];
+            double pb = 0.0;
+            bool found = false;
+            if (f & 2u) found = pair_find(key_xor(K, g), a.keys_s, a.b_s, a.tab, tag, &pb);
+            const double a1 = __dmul_rn(c, g.ch);                    // cosh(theta) P
+            const double sum = __dadd_rn(a1, pb);                     // + the partner's child
+            const double va = !(f & 2u) ? c : (found ? sum : a1);     // {P,Q} = 0: unchanged
+            const bool emit_b = (f & 2u) && !found;
+            // threshold and weight cutoff on the merged children (Sec. II.B)
+            bool keep_a = above(va, dbits) && light(K, g.maxw);
+            const bool keep_b = emit_b && above(a.b_s[i], dbits) && light(key_xor(K, g), g.maxw);
+            if (key_is_zero(K)) {
+                ctl->norm[nxt] = va;
+                if (!keep_a) set_status(ctl, ST_TRACE_ZERO, 1);
+                keep_a = true;
+            }
+            vals[i] = va;
+            o = (keep_a ? 1u : 0u) | (keep_b ? 2u : 0u);
+        }
+        a.flags_s[i] = (uint8_t)o;
+        cnt += __popc(o);
+    }
+    uint32_t tot;
+    const uint32_t off = block_scan_1bar<BLOCK>(cnt, a.s_warp, &tot);   // (2)
+    // the caller's room starts at base (the same on every thread)
+    uint64_t pos = base + off;
+    // write pass: warp-uniform rounds (the candidate list is filled warp-wide)
+    for (uint32_t i0 = 0; i0 < n; i0 += BLOCK) {
+        const uint32_t i = i0 + threadIdx.x;
+        uint32_t o = 0;
+        PKey<W> K;
+#pragma unroll
+        for (int w = 0; w < W; ++w) { K.x[w] = 0; K.z[w] = 0; }
+        double va = 0.0, b = 0.0;
+        if (i < n) {
+            o = a.flags_s[i];
+            if (o) {
+                K = a.keys_s[i];
+                va = vals[i];
+                b = a.b_s[i];
+            }
+        }
+        stage_emit(K, va, b, o, g, kout, cout, pos, st, cd, a.s_cn);
+        pos += __popc(o);
+    }
+    __syncthreads();                                                  // (3) staging free
+    return tot;
+}
+
+// The tag of the next pass (every thread calls it): slots hold 16-bit tags,
+// so after 65535 passes of one CTA the table is cleared and tags restart.
+template <int W, int BLOCK>
+__device__ __forceinline__ uint32_t next_tag(uint32_t tag, uint32_t* tab) {
+    if (tag < 0xffffu) return tag + 1u;
+    for (uint32_t k = threadIdx.x; k < (uint32_t)StageGeom<W>::kSlots; k += BLOCK) tab[k] = 0u;
+    __syncthreads();
+    return 1u;
+}
+
+template <int W, int BLOCK>
+struct PartOcc {
+    // CTAs per SM the launch bound asks for: the staging and table take
+    // Stage<W>::kBytes of shared memory per CTA
+    static constexpr int kMin = BLOCK <= 256 ? 5 : 2;
+};
+
+// The gate's merge, one partition at a time per CTA.  The partition comes
+// from the scatter buffer (fixed stride, cursor) or is a segment the
+// previous gate of the window wrote (descriptor).  It is copied into shared
+// memory by two bulk (TMA) copies, keys and coefficients, completed on an
+// mbarrier; a later partition of the same CTA has been prefetched into L2.
+// One pass (stage_pass) then merges it, and its kept children go to one
+// contiguous segment of the CTA's output chunk, recorded as the partition's
+// descriptor for the next gate.  Chunks are claimed from the buffer's
+// allocator a few hundred partitions at a time, so no partition waits on a
+// global atomic.  A partition above the staging capacity is merged in
+// sub-passes: each gathers the strings of one hash class of the key with
+// the gate's sites cleared (which K and Q.K share) into the staging arrays.
+template <int W, int BLOCK>
+__global__ void __launch_bounds__(BLOCK, (PartOcc<W, BLOCK>::kMin))
 k_gate_part(const PKey<W>* __restrict__ pk, const double* __restrict__ pc,
             unsigned int* __restrict__ cursor, uint64_t pbuf_cap, PartDesc* desc0,
             PartDesc* desc1, Bufs<W> B, DevCtl* ctl, GateArg<W> g, double delta,
-            uint64_t cap_out) {
+            uint64_t cap_out, uint64_t chunk, CandRegions cd, ChunkDesc* chunks0,
+            ChunkDesc* chunks1, uint32_t max_chunks) {
+    using G = Stage<W>;
+    constexpr uint32_t C = G::C, S = G::S;
     extern __shared__ __align__(16) unsigned char smem[];
-    constexpr int S = PartGeom<W>::kSlots;
-    constexpr uint64_t CHUNK = (uint64_t)kPBlock * kPIpt;
-    // a segment above this size makes the next gate re-partition: the
-    // shared table's limit, or twice the register chunk for small CTAs
-    constexpr uint32_t kSplitAt = (uint32_t)(2 * CHUNK) < (uint32_t)PartGeom<W>::kSplit
-                                      ? (uint32_t)(2 * CHUNK) : (uint32_t)PartGeom<W>::kSplit;
-    PKey<W>* t_keys = reinterpret_cast<PKey<W>*>(smem);
-    double* t_b = reinterpret_cast<double*>(t_keys + S);
-    uint32_t* t_tag = reinterpret_cast<uint32_t*>(t_b + S);
-    __shared__ uint32_t s_warp[kPBlock / 32];
-    __shared__ uint32_t s_scan[kPBlock / 32];
-    __shared__ unsigned long long s_base;
-    __shared__ uint32_t s_total;
-    if (ctl->status) return;
+    __shared__ uint32_t s_warp[BLOCK / 32];
+    __shared__ __align__(8) uint64_t s_bar;
+    __shared__ unsigned long long s_chunk, s_chsz, s_nout, s_range[2];
+    __shared__ uint32_t s_cn, s_long, s_n;
+    __shared__ int s_stop;
+    __shared__ Pending<W> s_pd;
+    __shared__ double s_rnorm;
+    const PassArgs<W> pa{reinterpret_cast<PKey<W>*>(smem + G::kKeys),
+                         reinterpret_cast<double*>(smem + G::kVals),
+                         reinterpret_cast<double*>(smem + G::kB),
+                         reinterpret_cast<uint32_t*>(smem + G::kTab), smem + G::kFlags, s_warp,
+                         &s_cn};
     const int cur = ctl->cur, nxt = cur ^ 1;
     const bool from_scatter = ctl->part_from_scatter != 0;
     const uint32_t P = ctl->part_P;
@@ -425,22 +641,70 @@ k_gate_part(const PKey<W>* __restrict__ pk, const double* __restrict__ pc,
     const PartDesc* __restrict__ din = cur ? desc1 : desc0;
     PartDesc* __restrict__ dout = cur ? desc0 : desc1;
     const unsigned long long dbits = (unsigned long long)__double_as_longlong(delta);
-    // the normaliser and the deferred select's kept set are read from shared
-    // memory where they are applied (once per item), not held in registers
-    // through the merge
-    __shared__ Pending<W> s_pd;
-    __shared__ double s_rnorm;
     if (threadIdx.x == 0) {
+        // one read of the status for the whole CTA (another CTA may set it
+        // meanwhile, and every thread must leave at the same point)
+        s_stop = ctl->status;
         s_pd = pending_of<W>(ctl);
         s_rnorm = ctl->rnorm[cur];
+        s_cn = 0u;
+        s_range[0] = ctl->sp_lo;
+        s_range[1] = ctl->sp_hi;
+        s_nout = 0ULL;      // thread 0 counts the CTA's output and long partitions
+        s_long = 0u;
+        mbar_init(&s_bar, 1);
     }
+    if (blockIdx.x == 0 && threadIdx.x == 0 && !ctl->status) {
+        ctl->cand_regions = gridDim.x;
+        ctl->seg = 1;          // the output is the P segments this merge writes
+        ctl->seg_P = P;
+    }
+    for (uint32_t k = threadIdx.x; k < S; k += BLOCK) pa.tab[k] = 0u;
+    __syncthreads();
+    if (s_stop) return;
     const Pending<W>& pd = s_pd;
-    const double& rnorm = s_rnorm;
+    const double rnorm = s_rnorm;
     PKey<W>* __restrict__ kout = B.key(nxt);
     double* __restrict__ cout = B.coef(nxt);
-    unsigned long long out_max = 0;   // largest |c| pattern written (top-M select range)
-    for (int s2 = threadIdx.x; s2 < S; s2 += kPBlock) t_tag[s2] = 0u;
-    __syncthreads();
+    SelStats st{s_range, 0ULL, 0u};
+    // this CTA's output chunk: [ch_start, ch_pos) written, [ch_pos, ch_end)
+    // free (the same on every thread)
+    unsigned long long ch_start = 0, ch_pos = 0, ch_end = 0;
+    uint32_t tag = 0, parity = 0;
+    ChunkDesc* __restrict__ chunks_out = cur ? chunks0 : chunks1;
+    // record the written run of a chunk for the readers of the whole state
+    auto record_chunk = [&](unsigned long long start, unsigned long long end) {
+        if (end == start) return;
+        const unsigned int q = atomicAdd(&ctl->nchunk[nxt], 1u);
+        if (q < max_chunks) {
+            chunks_out[q].off = start;
+            chunks_out[q].cnt = (unsigned int)(end - start);
+        } else {
+            set_status(ctl, ST_CAPACITY, 46);
+        }
+    };
+    // claim room for at least `need` terms (every thread calls it)
+    auto claim = [&](unsigned long long need) -> bool {
+        if (threadIdx.x == 0) {
+            record_chunk(ch_start, ch_pos);
+            const unsigned long long sz = need > chunk ? need : chunk;
+            const unsigned long long b = atomicAdd(&ctl->alloc[nxt], sz);
+            if (b + sz > cap_out) {
+                set_status(ctl, ST_CAPACITY, 2);
+                s_chunk = ~0ULL;
+            } else {
+                s_chunk = b;
+            }
+            s_chsz = sz;
+        }
+        __syncthreads();
+        const unsigned long long b = s_chunk;
+        if (b == ~0ULL) return false;
+        ch_start = b;
+        ch_pos = b;
+        ch_end = b + s_chsz;
+        return true;
+    };
     for (uint32_t p = blockIdx.x; p < P; p += gridDim.x) {
         const PKey<W>* kp;
         const double* cp;
@@ -457,127 +721,126 @@ k_gate_part(const PKey<W>* __restrict__ pk, const double* __restrict__ pc,
         }
         // warm L2 with the partition this CTA takes next
         const uint32_t pn = p + gridDim.x;
-        if (pn < P) {
+        if (threadIdx.x == 0 && pn < P) {
             uint64_t nn;
-            const char *nk, *nc;
+            const PKey<W>* nk;
+            const double* nc;
             if (from_scatter) {
                 nn = cursor[pn];
                 if (nn > R) nn = R;
-                nk = reinterpret_cast<const char*>(pk + (uint64_t)pn * R);
-                nc = reinterpret_cast<const char*>(pc + (uint64_t)pn * R);
+                nk = pk + (uint64_t)pn * R;
+                nc = pc + (uint64_t)pn * R;
             } else {
                 nn = din[pn].cnt;
-                nk = reinterpret_cast<const char*>(B.key(cur) + din[pn].off);
-                nc = reinterpret_cast<const char*>(B.coef(cur) + din[pn].off);
+                nk = B.key(cur) + din[pn].off;
+                nc = B.coef(cur) + din[pn].off;
             }
-            for (uint64_t b = (uint64_t)threadIdx.x * 128; b < nn * sizeof(PKey<W>); b += 128 * kPBlock)
-                asm volatile("prefetch.global.L2 [%0];" :: "l"(nk + b));
-            for (uint64_t b = (uint64_t)threadIdx.x * 128; b < nn * sizeof(double); b += 128 * kPBlock)
-                asm volatile("prefetch.global.L2 [%0];" :: "l"(nc + b));
+            if (nn) {
+                l2_prefetch_bulk(nk, nn * sizeof(PKey<W>));
+                l2_prefetch_bulk(nc, nn * sizeof(double));
+            }
         }
-        bool ok = true;
-        if (np <= CHUNK) {
-            // the whole partition in registers, items j*BLOCK + tid (coalesced)
-            PartItem<W> it[kPIpt];
-#pragma unroll
-            for (int j = 0; j < kPIpt; ++j) {
-                it[j] = part_item(kp, cp, (uint64_t)j * kPBlock + threadIdx.x, np, g, rnorm, pd, ctl);
-                if (it[j].comm) ok &= part_insert(it[j], t_keys, t_b, t_tag, p + 1u);
+        if (np <= C) {
+            // stage the partition: keys, and the coefficients from the 16-byte
+            // boundary at or below their start (one spare element when the
+            // segment starts at an odd element)
+            const uint32_t shift = (uint32_t)((reinterpret_cast<uint64_t>(cp) >> 3) & 1ULL);
+            if (np) {
+                if (threadIdx.x == 0) {
+                    const uint32_t kb = (uint32_t)(np * sizeof(PKey<W>));
+                    const uint32_t cb = (uint32_t)(((shift + np) * sizeof(double) + 15) & ~15ULL);
+                    fence_async_shared();
+                    mbar_expect(&s_bar, kb + cb);
+                    bulk_g2s(pa.keys_s, kp, kb, &s_bar);
+                    bulk_g2s(pa.vals_s, cp - shift, cb, &s_bar);
+                }
+                const bool ok = mbar_wait(&s_bar, parity, kWaitPolls);
+                if (__syncthreads_or(!ok)) {
+                    if (threadIdx.x == 0) {
+                        set_status(ctl, ST_TIMEOUT, 45);
+                        mbar_wait(&s_bar, parity, kWaitPolls);   // the copy in flight
+                    }
+                    __syncthreads();
+                    return;
+                }
+                parity ^= 1u;
             }
-            if (!ok) set_status(ctl, ST_CAPACITY, 41);
-            __syncthreads();                                   // (1) table built
             // every thread has read the cursor: leave it zero for the next scatter
             if (from_scatter && threadIdx.x == 0) cursor[p] = 0u;
-            double va[kPIpt];
-            uint32_t flags = 0, cnt = 0;
-#pragma unroll
-            for (int j = 0; j < kPIpt; ++j) {
-                const uint32_t fl =
-                    part_flags(it[j], g, t_keys, t_b, t_tag, p + 1u, dbits, ctl, nxt, &va[j]);
-                flags |= fl << (2 * j);
-                cnt += __popc(fl);
-            }
-            uint32_t tot;
-            const uint32_t off = scan_one_barrier<kPBlock>(cnt, s_warp, &tot);   // (2)
+            tag = next_tag<W, BLOCK>(tag, pa.tab);
+            // room: the partition's children (at most 2 np) fit a fresh chunk
+            if (ch_end - ch_pos < 2 * np && !claim(2 * np)) return;
+            const uint32_t tot = stage_pass<W, BLOCK>(pa, (uint32_t)np, shift, g, pd, rnorm, dbits,
+                                                      ctl, nxt, tag, kout, cout, st, cd, ch_pos);
             if (threadIdx.x == 0) {
-                const unsigned long long base =
-                    tot ? atomicAdd(&ctl->count[nxt], (unsigned long long)tot) : 0ULL;
-                s_base = base;
-                dout[p].off = base;
+                dout[p].off = ch_pos;
                 dout[p].cnt = tot;
-                if (tot > kSplitAt) ctl->part_over = 1;
+                s_nout += tot;
             }
-            __syncthreads();                                   // (3) segment claimed
-            const unsigned long long base = s_base;
-            if (base + tot > cap_out) {
-                if (threadIdx.x == 0) set_status(ctl, ST_CAPACITY, 2);
-                return;
-            }
-            uint64_t pos = base + off;
-#pragma unroll
-            for (int j = 0; j < kPIpt; ++j) {
-                const uint32_t fl = (flags >> (2 * j)) & 3u;
-                part_write(it[j], g, va[j], fl, kout, cout, pos);
-                pos += __popc(fl);
-                out_max = max(out_max, (fl & 1u) ? abs_pattern(va[j]) : 0ULL);
-                out_max = max(out_max, (fl & 2u) ? abs_pattern(it[j].b) : 0ULL);
-            }
+            ch_pos += tot;
         } else {
-            // a long partition: build the table, count its output, then
-            // recompute and write (every item reloaded each pass)
-            for (uint64_t i = threadIdx.x; i < np; i += kPBlock) {
-                const PartItem<W> x = part_item(kp, cp, i, np, g, rnorm, pd, ctl);
-                if (x.comm) ok &= part_insert(x, t_keys, t_b, t_tag, p + 1u);
+            // a long partition: k sub-passes over the hash classes of the key
+            // with the gate's sites cleared (about C/2 strings each); the
+            // partition's children stay one segment
+            const uint32_t k = (uint32_t)((2 * np + C - 1) / C);
+            if (ch_end - ch_pos < 2 * np && !claim(2 * np)) return;
+            const unsigned long long start = ch_pos;
+            for (uint32_t j = 0; j < k; ++j) {
+                if (threadIdx.x == 0) s_n = 0u;
+                __syncthreads();
+                for (uint64_t i = threadIdx.x; i < np; i += BLOCK) {
+                    const PKey<W> K = load_key_stream(kp + i);
+                    const double raw = __ldcs(cp + i);
+                    const bool live = !pd.on || cap_keep(K, raw, pd.T, pd.all_ties, pd.tk);
+                    if (!live) {
+                        if (key_is_zero(K)) set_status(ctl, ST_TRACE_ZERO, 43);
+                        continue;
+                    }
+                    const uint32_t cls = commutes(K, g) ? sub_pass(K, g, k) : (uint32_t)(i % k);
+                    if (cls != j) continue;
+                    const uint32_t q = atomicAdd(&s_n, 1u);
+                    if (q < C) {
+                        pa.keys_s[q] = K;
+                        pa.vals_s[q] = raw;
+                    } else {
+                        set_status(ctl, ST_CAPACITY, 44);
+                    }
+                }
+                __syncthreads();
+                if (j == 0 && from_scatter && threadIdx.x == 0) cursor[p] = 0u;
+                const uint32_t n = s_n < C ? s_n : C;
+                tag = next_tag<W, BLOCK>(tag, pa.tab);
+                ch_pos += stage_pass<W, BLOCK>(pa, n, 0u, g, pd, rnorm, dbits, ctl, nxt, tag, kout,
+                                               cout, st, cd, ch_pos);
             }
-            if (!ok) set_status(ctl, ST_CAPACITY, 41);
-            if (threadIdx.x == 0) s_total = 0u;
-            __syncthreads();
-            if (from_scatter && threadIdx.x == 0) cursor[p] = 0u;
-            for (uint64_t c0 = 0; c0 < np; c0 += kPBlock) {
-                const PartItem<W> x = part_item(kp, cp, c0 + threadIdx.x, np, g, rnorm, pd, ctl);
-                double va;
-                const uint32_t fl =
-                    part_flags(x, g, t_keys, t_b, t_tag, p + 1u, dbits, ctl, nxt, &va);
-                uint32_t tot;
-                block_exclusive_scan<kPBlock>(__popc(fl), &tot, s_scan);
-                if (threadIdx.x == 0) s_total += tot;
-            }
-            __syncthreads();
             if (threadIdx.x == 0) {
-                const uint32_t tot = s_total;
-                const unsigned long long base =
-                    tot ? atomicAdd(&ctl->count[nxt], (unsigned long long)tot) : 0ULL;
-                s_base = base;
-                dout[p].off = base;
-                dout[p].cnt = tot;
-                if (tot > kSplitAt) ctl->part_over = 1;
+                dout[p].off = start;
+                dout[p].cnt = (unsigned int)(ch_pos - start);
+                s_nout += ch_pos - start;
+                s_long += 1u;
             }
-            __syncthreads();
-            const unsigned long long base = s_base;
-            if (base + s_total > cap_out) {
-                if (threadIdx.x == 0) set_status(ctl, ST_CAPACITY, 2);
-                return;
-            }
-            uint64_t run = 0;
-            for (uint64_t c0 = 0; c0 < np; c0 += kPBlock) {
-                const PartItem<W> x = part_item(kp, cp, c0 + threadIdx.x, np, g, rnorm, pd, ctl);
-                double va;
-                const uint32_t fl =
-                    part_flags(x, g, t_keys, t_b, t_tag, p + 1u, dbits, ctl, nxt, &va);
-                uint32_t tot;
-                const uint32_t off = block_exclusive_scan<kPBlock>(__popc(fl), &tot, s_scan);
-                part_write(x, g, va, fl, kout, cout, base + run + off);
-                out_max = max(out_max, (fl & 1u) ? abs_pattern(va) : 0ULL);
-                out_max = max(out_max, (fl & 2u) ? abs_pattern(x.b) : 0ULL);
-                run += tot;
-            }
-            __syncthreads();   // the table is read until here
         }
     }
-    // one atomic per warp for the largest pattern
+    // one atomic per warp for the largest pattern and the count above the
+    // candidate range, one per CTA for the term count
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) out_max = max(out_max, __shfl_xor_sync(0xffffffffu, out_max, o));
-    if ((threadIdx.x & 31) == 0 && out_max) atomicMax(&ctl->out_max, out_max);
+    for (int o = 16; o > 0; o >>= 1) {
+        st.out_max = max(st.out_max, __shfl_xor_sync(0xffffffffu, st.out_max, o));
+        st.above += __shfl_xor_sync(0xffffffffu, st.above, o);
+    }
+    if ((threadIdx.x & 31) == 0) {
+        if (st.out_max) atomicMax(&ctl->out_max, st.out_max);
+        if (st.above) atomicAdd(&ctl->sp_above, (unsigned long long)st.above);
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        record_chunk(ch_start, ch_pos);
+        if (s_nout) atomicAdd(&ctl->count[nxt], s_nout);
+        if (s_long) atomicAdd(&ctl->stat_long, (unsigned long long)s_long);
+        const uint32_t c = s_cn;
+        cd.cnt[blockIdx.x] = c < cd.region ? c : (uint32_t)cd.region;
+        if (c > cd.region) ctl->sp_ovf = 1;
+    }
 }
 
 // ---------------------------------------------------------------------------
@@ -634,44 +897,41 @@ static cudaError_t scatter_w(const DeviceState& s, const HostGate& h, int force,
                                                reinterpret_cast<PKey<W>*>(s.part_keys),
                                                s.part_coef, s.part_cursor, s.part_cap,
                                                s.part_max, gate_of<W>(h), part_fn_of<W>(h), force,
-                                               s.n, s.part_target);
+                                               s.n, s.part_target, s.chunks[0], s.chunks[1]);
     return cudaGetLastError();
 }
 
-template <int W, int BLOCK, int IPT>
-static cudaError_t merge_wbi(const DeviceState& s, const GateArg<W>& g, cudaStream_t st) {
+template <int W, int BLOCK>
+static cudaError_t merge_wb(const DeviceState& s, const GateArg<W>& g, cudaStream_t st) {
     static int per_sm = 0;
+    constexpr size_t smem = Stage<W>::kBytes;
     if (!per_sm) {
-        cudaFuncSetAttribute(k_gate_part<W, BLOCK, IPT>,
-                             cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)part_smem_bytes<W>());
-        // shared memory for every resident CTA's table rather than L1
-        cudaFuncSetAttribute(k_gate_part<W, BLOCK, IPT>,
-                             cudaFuncAttributePreferredSharedMemoryCarveout,
+        cudaFuncSetAttribute(k_gate_part<W, BLOCK>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)smem);
+        // shared memory for every resident CTA's staging rather than L1
+        cudaFuncSetAttribute(k_gate_part<W, BLOCK>, cudaFuncAttributePreferredSharedMemoryCarveout,
                              (int)cudaSharedmemCarveoutMaxShared);
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_gate_part<W, BLOCK, IPT>, BLOCK,
-                                                      part_smem_bytes<W>());
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_gate_part<W, BLOCK>, BLOCK, smem);
         if (per_sm < 1) per_sm = 1;
     }
-    k_gate_part<W, BLOCK, IPT><<<s.num_sms * per_sm, BLOCK, part_smem_bytes<W>(), st>>>(
+    int grid = s.num_sms * per_sm;
+    if (grid > s.max_ctas) grid = s.max_ctas;   // one candidate region per CTA
+    k_gate_part<W, BLOCK><<<grid, BLOCK, smem, st>>>(
         reinterpret_cast<const PKey<W>*>(s.part_keys), s.part_coef, s.part_cursor, s.part_cap,
-        s.part_desc[0], s.part_desc[1], pbufs_of<W>(s), s.ctl, g, s.delta, s.buf_cap);
+        s.part_desc[0], s.part_desc[1], pbufs_of<W>(s), s.ctl, g, s.delta, s.buf_cap, s.chunk,
+        s.cand, s.chunks[0], s.chunks[1], s.max_chunks);
     return cudaGetLastError();
 }
 
+// The partitioned merge's CTA size (threads loop over a partition's staged
+// strings, so there is no items-per-thread parameter on this path).
 template <int W>
 static cudaError_t merge_w(const DeviceState& s, const HostGate& h, cudaStream_t st) {
     const GateArg<W> g = gate_of<W>(h);
-    switch (s.block * 16 + s.ipt) {
-        case 128 * 16 + 1: return merge_wbi<W, 128, 1>(s, g, st);
-        case 128 * 16 + 2: return merge_wbi<W, 128, 2>(s, g, st);
-        case 128 * 16 + 4: return merge_wbi<W, 128, 4>(s, g, st);
-        case 256 * 16 + 1: return merge_wbi<W, 256, 1>(s, g, st);
-        case 256 * 16 + 2: return merge_wbi<W, 256, 2>(s, g, st);
-        case 256 * 16 + 4: return merge_wbi<W, 256, 4>(s, g, st);
-        case 512 * 16 + 1: return merge_wbi<W, 512, 1>(s, g, st);
-        case 512 * 16 + 2: return merge_wbi<W, 512, 2>(s, g, st);
-        case 512 * 16 + 4: return merge_wbi<W, 512, 4>(s, g, st);
+    switch (s.block) {
+        case 128: return merge_wb<W, 128>(s, g, st);
+        case 256: return merge_wb<W, 256>(s, g, st);
+        case 512: return merge_wb<W, 512>(s, g, st);
         default: return cudaErrorInvalidValue;
     }
 }
@@ -720,6 +980,21 @@ void plan_windows(int W, std::vector<HostGate>& gates) {
         }
         k = e;
     }
+}
+
+// A merge CTA claims output room in chunks of about an eighth of its share
+// of a bounded state (at most 2^16 terms); what the chunks leave unused is at
+// most one chunk per CTA plus the tails a partition that did not fit left
+// behind, which the state buffers' slack covers.
+uint64_t merge_chunk(uint64_t cap_M, int max_ctas) {
+    uint64_t c = cap_M / (8ULL * (uint64_t)(max_ctas > 0 ? max_ctas : 1));
+    uint64_t p = 16;
+    while (p * 2 <= c && p < (1ULL << 16)) p *= 2;
+    return p;
+}
+
+uint64_t merge_slack(uint64_t cap_M, int max_ctas) {
+    return 2ULL * (uint64_t)max_ctas * merge_chunk(cap_M, max_ctas) + cap_M / 4 + 4096;
 }
 
 int partition_target_default(int W) {

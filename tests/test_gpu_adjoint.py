@@ -104,3 +104,24 @@ def test_autograd_energy_gradient_wrt_fields_and_couplings():
     assert abs(float(energy) - f_o) <= 1e-12 * abs(f_o)
     _close(Jv.grad.numpy(), want_J)
     _close(hv.grad.numpy(), want_h)
+
+
+@pytest.mark.parametrize("obs_kind", ["energy", "zz"])
+def test_adjoint_cfg5_size_prefix_matches_oracle(obs_kind):
+    """The gradient workload at its own size (n = 32, 63 parameters, per-site
+    fields and couplings from its seed, dtau = 0.02, |c| <= 1e-7 dropped) on a
+    two-layer prefix with at most 2^14 terms (top-M, the frozen support of a
+    step is its kept set): GPU adjoint against the oracle's, 1e-10 of the
+    largest component, for d<H>/d alpha and d<Z15 Z16>/d alpha."""
+    w = wl.WORKLOADS["adjoint_n32"]
+    H = w.H
+    O = w.observables["energy"] if obs_kind == "energy" else w.observables["Z15Z16"]
+    M, layers = 1 << 14, 2
+    g = itpp.Propagator(H.n, H.gate_x, H.gate_z, H.alpha, w.dtau, w.delta, M, 1)
+    f_g, d_g = g.adjoint(layers, O, ckpt_every=1)
+    assert g.stats()["cap_events"] > 0
+    o = oracle.Oracle(H.n, H.gate_x, H.gate_z, H.alpha, w.dtau, w.delta, M, 1)
+    f_o, d_o = oracle.FrozenAdjoint(o, layers).grad_alpha(O, H.n_gates)
+    assert abs(f_g - f_o) <= 1e-12 * max(1.0, abs(f_o))
+    assert H.n_gates == 63
+    _close(d_g, d_o)
