@@ -97,6 +97,12 @@ def parse():
     ap.add_argument("--kscan-betas", default="0.08,0.24,0.8")
     ap.add_argument("--kscan-budget", type=float, default=900.0,
                     help="seconds of the K-truncation scan (--mode kscan)")
+    ap.add_argument("--record-traffic", default="",
+                    help="an ncu launch-list CSV (gpu__time_duration.sum, dram__bytes_read.sum, "
+                         "dram__bytes_write.sum) of the headline command: write the merge "
+                         "kernel's DRAM bytes per launch to profiles/traffic.json and exit")
+    ap.add_argument("--traffic-command", default="",
+                    help="the ncu command that wrote the CSV (recorded beside the bytes)")
     return ap.parse_args()
 
 
@@ -286,9 +292,11 @@ def run_reference(args, w):
 def measure_batch(args, layers, cap_log2, check_instances=8, autotune=True):
     """64 independent open chains (the field-sweep recipe: n ~ U{16..64},
     h ~ U[0.5, 2], seed 14400; J = 1, dtau = 0.02, delta = 1e-7, at most
-    2^cap_log2 terms each, top-M), batched (one graph launch per layer)
-    against the same 64 propagations run one after another as plain runs.
-    Returns the record (with the clocks sampled during both timings)."""
+    2^cap_log2 terms each, top-M), batched (one graph launch per layer, the
+    partitioned merge; the global-table batch timed beside it) against the
+    same 64 propagations run one after another as plain runs.  Returns the
+    record (with the clocks sampled during the partitioned batch and the
+    plain runs)."""
     import torch
     import paper_2601_14400_gb300 as itpp
     ns, hs = wl.batch_field_sweep()
@@ -296,11 +304,23 @@ def measure_batch(args, layers, cap_log2, check_instances=8, autotune=True):
     dtau, delta, M, L = 0.02, 1e-7, 1 << cap_log2, layers
     stream = torch.cuda.Stream()
     clocks = ClockSampler(torch.cuda.current_device())
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    # the global-table batch (merge_path 2) first, for comparison
+    bt = itpp.BatchPropagator(hams, dtau, delta, M, cap_policy=1, stream=stream, merge_path=2)
+    tune_table = bt.autotune(probe_layers=2) if autotune else None
+    torch.cuda.synchronize()
+    e0.record(stream)
+    bt.apply_trotter_layer(L)
+    e1.record(stream)
+    bt.synchronize()
+    t_table = e0.elapsed_time(e1)
+    counts_t, _ = bt.counts()
+    bt.close()
+    # the partitioned batch (merge_path 0), the figure reported
     bp = itpp.BatchPropagator(hams, dtau, delta, M, cap_policy=1, stream=stream)
     tune = bp.autotune(probe_layers=2) if autotune else None
     torch.cuda.synchronize()
     clocks.start()
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e0.record(stream)
     bp.apply_trotter_layer(L)
     e1.record(stream)
@@ -332,13 +352,16 @@ def measure_batch(args, layers, cap_log2, check_instances=8, autotune=True):
                            np.array_equal(pc.view(np.uint64), bc[order].view(np.uint64)))
         g.close()
     clk = clocks.stop()
-    same = (list(map(int, counts_b)) == counts_p) and bool(same_terms)
+    same = (list(map(int, counts_b)) == counts_p and list(map(int, counts_t)) == counts_p
+            and bool(same_terms))
     return {"metric": "batched vs plain: Pauli terms/s per Trotter gate",
             "value": terms_b / (t_batch * 1e-3), "unit": UNIT,
             "plain_value": terms_p / (t_plain * 1e-3), "speedup": t_plain / t_batch,
-            "batched_ms": t_batch, "plain_ms": t_plain, "identical_results": bool(same),
+            "batched_ms": t_batch, "plain_ms": t_plain,
+            "global_table_batched_ms": t_table, "speedup_over_global_table": t_table / t_batch,
+            "identical_results": bool(same),
             "instances_compared_bitwise": len(chk), "cap_events": int(cap_events),
-            "autotune": tune, "clocks": clk,
+            "autotune": tune, "autotune_global_table": tune_table, "clocks": clk,
             "config": {"workload": "field sweep: 64 open TFIM chains, n~U{16..64}, "
                                    "h~U[0.5,2], J=1 (seed 14400)", "dtau": dtau,
                        "delta": delta, "cap_M": M, "cap_policy": "top-M", "layers": L,
@@ -734,8 +757,47 @@ def measure_cfg3(args, timed_layers=2, max_setup=6):
     return rec
 
 
+def record_traffic(args):
+    """DRAM bytes per launch of the partition merge from an ncu CSV launch
+    list (one row per launch and metric), stored with the digest of the
+    merge's sources so that the headline line drops it once they change."""
+    import csv
+    rows = {}
+    with open(args.record_traffic, newline="") as f:
+        lines = [ln for ln in f if ln.startswith('"')]
+    for r in csv.DictReader(lines):
+        if "k_gate_part" not in r.get("Kernel Name", ""):
+            continue
+        d = rows.setdefault(r["ID"], {})
+        v = float(r["Metric Value"].replace(",", ""))
+        unit = r.get("Metric Unit", "")
+        scale = {"byte": 1, "Kbyte": 1e3, "Mbyte": 1e6, "Gbyte": 1e9,
+                 "nsecond": 1, "usecond": 1e3, "msecond": 1e6}.get(unit, 1)
+        d[r["Metric Name"]] = v * scale
+    launches = [rows[k] for k in sorted(rows, key=int)
+                if "dram__bytes_read.sum" in rows[k] and "dram__bytes_write.sum" in rows[k]]
+    if not launches:
+        print(json.dumps({"error": "no k_gate_part launch with DRAM bytes in "
+                          + args.record_traffic}))
+        return 1
+    tot = [d["dram__bytes_read.sum"] + d["dram__bytes_write.sum"] for d in launches]
+    rec = {"kernel_class": 1, "kernel": "k_gate_part", "source_digest": source_digest(),
+           "bytes_per_launch": sum(tot) / len(tot), "launches_measured": len(tot),
+           "first_launches": [{"dram_read": int(d["dram__bytes_read.sum"]),
+                               "dram_write": int(d["dram__bytes_write.sum"]),
+                               "duration_ns": int(d.get("gpu__time_duration.sum", 0))}
+                              for d in launches[:4]],
+           "workload": args.workload, "command": args.traffic_command}
+    with open(os.path.join(ROOT, "profiles", "traffic.json"), "w") as f:
+        json.dump(rec, f, indent=2)
+    print(json.dumps({"bytes_per_launch": rec["bytes_per_launch"], "launches": len(tot)}))
+    return 0
+
+
 def main():
     args = parse()
+    if args.record_traffic:
+        return record_traffic(args)
     if args.mode == "batch":
         return run_batch(args)
     if args.mode == "adjoint":
@@ -956,7 +1018,8 @@ def main():
 
 # the sources of the partition merge kernel (k_gate_part): its recorded DRAM
 # traffic stays valid while these are unchanged
-MERGE_SOURCES = ("itpp_part.cu", "itpp_common.cuh", "itpp_gate_body.cuh", "itpp_launch.h")
+MERGE_SOURCES = ("itpp_part.cu", "itpp_stage.cuh", "itpp_common.cuh", "itpp_gate_body.cuh",
+                 "itpp_launch.h")
 
 
 def source_digest(files=MERGE_SOURCES):

@@ -342,6 +342,21 @@ itpp_status itpp_adjoint(itpp_handle h, int n_layers, int ckpt_every, const uint
                          const uint64_t* obs_z, const double* w, int m, double* grad_alpha,
                          double* value);
 
+/* The frozen-support forward that itpp_adjoint differentiates, evaluated at
+ * other coefficients: the kept support of every step is the one the handle's
+ * own coefficients produce (as in itpp_adjoint), and the linear maps of the
+ * propagation rule (Eq. (ITPP_PropRules)) and the per-step trace
+ * normalisation (Sec. II.C) on it are applied with
+ * theta = alpha_eval[k] * dtau.  value receives f = sum_j w_j c_{P_j} after
+ * n_layers layers from the identity.  The paper has no counterpart: this is
+ * the function whose derivative at alpha_eval = alpha the adjoint returns,
+ * so that a central difference of it checks the gradient at any size.
+ * alpha_eval: host, one finite value per Hamiltonian term.  Other arguments,
+ * memory, state and synchronisation as itpp_adjoint. */
+itpp_status itpp_frozen_value(itpp_handle h, int n_layers, int ckpt_every,
+                              const double* alpha_eval, const uint64_t* obs_x,
+                              const uint64_t* obs_z, const double* w, int m, double* value);
+
 /* ---------------------------------------------------------------------------
  * Batched propagation: many independent instances in shared launches
  * ------------------------------------------------------------------------- */
@@ -350,7 +365,11 @@ itpp_status itpp_adjoint(itpp_handle h, int n_layers, int ckpt_every, const uint
  * together: in every Trotter layer, gate g of every instance that has one
  * runs in the same kernel launches, and the whole layer is one CUDA graph
  * launch.  Each instance's state is bit-identical to a plain run of the same
- * Hamiltonian with the same parameters.
+ * Hamiltonian with the same parameters.  p->merge_path 0 (default): every
+ * gate scatters each instance's terms into hash partitions of its pair key
+ * and merges the partitions of all instances in one launch of the
+ * shared-memory merge (p->partition_target as in itpp_create); 2: one global
+ * merge table per instance; 1 is not offered for batches (ITPP_ERR_ARG).
  *   B            1..65535 instances.
  *   n[B]         sites per instance (1..128); all instances use
  *                W = ceil(max n / 64) mask words.
@@ -363,7 +382,8 @@ itpp_status itpp_adjoint(itpp_handle h, int n_layers, int ckpt_every, const uint
  *   cuda_stream  stream to run on; NULL makes the library create its own
  *                (graph capture needs a non-legacy stream).
  * Memory: per instance two buffers of 2*cap_M terms, a table and a control
- * block (about 0.6 MB).  Errors: as itpp_create. */
+ * block (about 0.6 MB), and for merge_path 0 a scatter buffer of about
+ * 2.5*cap_M terms.  Errors: as itpp_create. */
 itpp_status itpp_batch_create(int B, const int* n, const int* n_gates, const uint64_t* gate_x,
                               const uint64_t* gate_z, const double* alpha, double dtau,
                               const itpp_params* p, void* cuda_stream, itpp_batch_handle* out);
@@ -376,12 +396,17 @@ itpp_status itpp_batch_apply_trotter_layer(itpp_batch_handle h, int n_layers);
 /* Wait; ITPP_OK if every instance is healthy, else the first error. */
 itpp_status itpp_batch_synchronize(itpp_batch_handle h);
 
-/* The launch shape and hash sizing of a batch, chosen by timing (the
- * autotuner of the batched path).  Tuned: threads per CTA of the
- * branch-emit kernel (128, 256, 512; two terms per thread), its CTAs per SM
- * (2, 4, 8), the table build's CTAs per SM (4, 8, 16) and the merge table's
- * highest load (25..65 %; itpp_batch_create with table_load_pct 0 sizes the
- * tables for 25 %, otherwise loads below the requested one are not tried).
+/* The launch shape of a batch, chosen by timing (the autotuner of the
+ * batched path).  Partitioned merge (merge_path 0): threads per CTA of the
+ * partition merge (128, 256, 512), its CTAs per SM (2, 4, or as many as fit),
+ * the scatter's CTAs per SM (4, 8, 16) and the mean partition size (350,
+ * 500, 700, 1000 terms at W = 1; 150, 300, 450 at W = 2; not tried when
+ * itpp_batch_create was given a partition_target).  Global table
+ * (merge_path 2): threads per CTA of the branch-emit kernel (128, 256, 512;
+ * two terms per thread), its CTAs per SM (2, 4, 8), the table build's CTAs
+ * per SM (4, 8, 16) and the merge table's highest load (25..65 %;
+ * itpp_batch_create with table_load_pct 0 sizes the tables for 25 %,
+ * otherwise loads below the requested one are not tried).
  * Each candidate is timed with CUDA events over probe_layers Trotter layers
  * from the identity, replayed as the layer graph; coordinate descent from
  * the default shape, one parameter at a time.  The fastest shape stays
@@ -391,14 +416,17 @@ itpp_status itpp_batch_synchronize(itpp_batch_handle h);
  *   probe_layers  >= 1.
  *   out           host, may be NULL. */
 typedef struct {
-    int main_block;              /* threads per CTA of the branch-emit kernel   */
+    int main_block;              /* threads per CTA of the merge kernel          */
     int main_grid;               /* its CTAs per SM                              */
-    int insert_grid;             /* CTAs per SM of the table build               */
-    int table_load_pct;          /* highest load of every instance's table (%)   */
+    int insert_grid;             /* CTAs per SM of the scatter / table build     */
+    int table_load_pct;          /* global table: highest load (%); else 0       */
     double ms_per_probe;         /* the chosen shape: probe_layers layers (ms)   */
-    double ms_per_probe_default; /* the default shape (256, 4, 8, 50 %)          */
+    double ms_per_probe_default; /* the default shape (partitioned: 256 threads,
+                                  * as many CTAs as fit, 8, the default size;
+                                  * global table: 256, 4, 8, 50 %)              */
     int candidates;              /* shapes timed                                 */
-    int reserved[3];
+    int partition_target;        /* partitioned: mean partition size; else 0     */
+    int reserved[2];
 } itpp_tune_result;
 itpp_status itpp_batch_autotune(itpp_batch_handle h, int probe_layers, itpp_tune_result* out);
 

@@ -61,7 +61,8 @@ class itpp_tune_result(ctypes.Structure):
     _fields_ = [("main_block", ctypes.c_int), ("main_grid", ctypes.c_int),
                 ("insert_grid", ctypes.c_int), ("table_load_pct", ctypes.c_int),
                 ("ms_per_probe", ctypes.c_double), ("ms_per_probe_default", ctypes.c_double),
-                ("candidates", ctypes.c_int), ("reserved", ctypes.c_int * 3)]
+                ("candidates", ctypes.c_int), ("partition_target", ctypes.c_int),
+                ("reserved", ctypes.c_int * 2)]
 
 
 _SIGNATURES = [
@@ -91,6 +92,8 @@ _SIGNATURES = [
     ("itpp_reset", ctypes.c_int, [_vp]),
     ("itpp_adjoint", ctypes.c_int, [_vp, ctypes.c_int, ctypes.c_int, _u64p, _u64p, _f64p,
                                     ctypes.c_int, _f64p, _f64p]),
+    ("itpp_frozen_value", ctypes.c_int, [_vp, ctypes.c_int, ctypes.c_int, _f64p, _u64p, _u64p,
+                                         _f64p, ctypes.c_int, _f64p]),
     ("itpp_batch_create", ctypes.c_int, [ctypes.c_int, _i32p, _i32p, _u64p, _u64p, _f64p,
                                          ctypes.c_double, ctypes.POINTER(itpp_params), _vp,
                                          ctypes.POINTER(_vp)]),
@@ -357,6 +360,19 @@ class Propagator:
                "itpp_adjoint")
         return f.value, g
 
+    def frozen_value(self, n_layers, obs, alpha_eval, ckpt_every=10):
+        """f = sum_j w_j c_{P_j} of the frozen-support forward (the support of
+        this handle's coefficients) evaluated at alpha_eval; see include/itpp.h."""
+        ox, pox = _u64(obs.x)
+        oz, poz = _u64(obs.z)
+        ow, pow_ = _f64(obs.w)
+        al, pal = _f64(np.asarray(alpha_eval, dtype=np.float64))
+        f = ctypes.c_double()
+        _check(lib().itpp_frozen_value(self._h, int(n_layers), int(ckpt_every), pal, pox, poz,
+                                       pow_, int(ow.shape[0]), ctypes.byref(f)),
+               "itpp_frozen_value")
+        return f.value
+
     def profile_enable(self, on=True):
         _check(lib().itpp_profile_enable(self._h, 1 if on else 0), "itpp_profile_enable")
 
@@ -372,7 +388,7 @@ class BatchPropagator:
     """B independent ITPP propagations advanced in shared launches."""
 
     def __init__(self, hams, dtau, delta, cap_M, cap_policy=0, stream=None, table_load_pct=0,
-                 max_weight=0):
+                 max_weight=0, merge_path=0, partition_target=0):
         self.B = len(hams)
         self.ns = [int(H.n) for H in hams]
         self.W = (max(self.ns) + 63) // 64
@@ -391,6 +407,8 @@ class BatchPropagator:
         p.cap_policy = int(cap_policy)
         p.table_load_pct = int(table_load_pct)
         p.max_weight = int(max_weight)
+        p.merge_path = int(merge_path)
+        p.partition_target = int(partition_target)
         h = _vp()
         st = lib().itpp_batch_create(self.B, n.ctypes.data_as(_i32p), ng.ctypes.data_as(_i32p),
                                      pgx, pgz, pal, float(dtau), ctypes.byref(p),
@@ -410,8 +428,9 @@ class BatchPropagator:
             pass
 
     def autotune(self, probe_layers=2):
-        """Time launch shapes and table loads on this batch, keep the fastest
-        (every instance is reset to the identity).  Returns the choice."""
+        """Time launch shapes (and partition sizes or table loads) on this
+        batch, keep the fastest (every instance is reset to the identity).
+        Returns the choice."""
         r = itpp_tune_result()
         _check(lib().itpp_batch_autotune(self._h, int(probe_layers), ctypes.byref(r)),
                "itpp_batch_autotune")

@@ -337,6 +337,62 @@ __global__ void k_adj_gen_copy(DevCtl* dst, const DevCtl* src) {
     if (threadIdx.x == 0) dst->gen = src->gen + 1u;
 }
 
+// Frozen forward with other gate weights: one step of the linear map of
+// Eq. (ITPP_PropRules) on the kept support recorded by the recompute (the
+// output positions of every input's children, and which were kept), before
+// the step's normalisation.  Every kept position receives exactly one write.
+template <int W>
+__global__ void __launch_bounds__(256)
+k_frz_step(const PKey<W>* kin, const double* u_in, uint64_t n_in, const int* self_out,
+           const int* emit_out, const int* part_src, const int* cmap, GateArg<W> g,
+           double* u_out) {
+    for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n_in;
+         i += (uint64_t)gridDim.x * blockDim.x) {
+        const PKey<W> K = kin[i];
+        const double u = u_in[i];
+        const int so = self_out[i];
+        const int ks = so >= 0 ? cmap[so] : -1;
+        if (!commutes(K, g)) {
+            if (ks >= 0) u_out[ks] = u;
+            continue;
+        }
+        const double m = product_negative(K, g) ? -g.msh : g.msh;   // s (-sinh)
+        const int ps = part_src[i];
+        const double a = __dmul_rn(g.ch, u);
+        if (ks >= 0) u_out[ks] = ps >= 0 ? __dadd_rn(a, __dmul_rn(m, u_in[ps])) : a;
+        const int eo = emit_out[i];
+        const int ke = eo >= 0 ? cmap[eo] : -1;
+        if (ke >= 0) u_out[ke] = __dmul_rn(m, u);
+    }
+}
+
+// The step's normalisation: every kept value divided by the identity's (the
+// identity then exactly one).  d receives the identity's value first.
+__global__ void k_frz_trace(const double* u, const unsigned long long* id_pos, double* d) {
+    if (threadIdx.x == 0 && blockIdx.x == 0) *d = u[*id_pos];
+}
+
+__global__ void __launch_bounds__(256)
+k_frz_scale(double* u, uint64_t n, const unsigned long long* id_pos, const double* d) {
+    const unsigned long long id = *id_pos;
+    const double r = __ddiv_rn(1.0, *d);
+    for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+         i += (uint64_t)gridDim.x * blockDim.x)
+        u[i] = i == id ? 1.0 : __dmul_rn(u[i], r);
+}
+
+// sum_i mu[i] u[i] (block partials; fixed grid, fixed order).
+__global__ void __launch_bounds__(kRB)
+k_frz_dot(const double* mu, const double* u, uint64_t n, double* partials) {
+    __shared__ double s[kRB];
+    double acc = 0.0;
+    for (uint64_t j = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; j < n;
+         j += (uint64_t)gridDim.x * blockDim.x)
+        acc = __dadd_rn(acc, __dmul_rn(mu[j], u[j]));
+    const double b = block_sum(acc, s);
+    if (threadIdx.x == 0) partials[blockIdx.x] = b;
+}
+
 // grad_alpha[k] = dtau * sum over layers of df/dtheta at gate k.
 __global__ void k_adj_params(const double* gstep, int n_layers, int n_gates, double dtau,
                              double* grad) {
@@ -355,9 +411,18 @@ struct DevBuf {
     template <class T> T* as() const { return static_cast<T*>(p); }
 };
 
+// Weights of a frozen evaluation: per elementary gate of the schedule.
+struct FrozenEval {
+    std::vector<double> ch, msh;
+};
+
+// The adjoint sweep (ev == nullptr), or the frozen forward evaluated with the
+// weights of ev on the support the handle's own coefficients produce (ev:
+// value receives f, grad_alpha is not written).
 template <int W>
 itpp_status adjoint_w(itpp_ctx* h, int L, int K, const uint64_t* obs_x, const uint64_t* obs_z,
-                      const double* seed, int m, double* grad_alpha, double* value) {
+                      const double* seed, int m, double* grad_alpha, double* value,
+                      const FrozenEval* ev = nullptr) {
     DeviceState& s = h->s;
     cudaStream_t st = h->stream;
     const int G = (int)h->gates.size();
@@ -471,7 +536,17 @@ itpp_status adjoint_w(itpp_ctx* h, int L, int K, const uint64_t* obs_x, const ui
     double* mu_cur = mu0.as<double>();
     double* mu_prev = mu1.as<double>();
 
-    for (int j = n_seg - 1; j >= 0; --j) {
+    // frozen evaluation: the state carried across segment boundaries (on
+    // the next snapshot's order) and the identity's value of a step
+    DevBuf u_snap, d_tr;
+    if (ev && (!u_snap.alloc(reg_max * 8) || !d_tr.alloc(64))) return ITPP_ERR_ALLOC;
+    if (ev) {
+        const double one = 1.0;   // segment 0 starts from the identity alone
+        if (!chk(cudaMemcpyAsync(u_snap.p, &one, 8, cudaMemcpyHostToDevice, st)))
+            return ITPP_ERR_CUDA;
+    }
+    for (int jj = 0; jj < n_seg; ++jj) {
+        const int j = ev ? jj : n_seg - 1 - jj;
         const long long s0 = (long long)j * K * G;
         const long long s1 = ((long long)(j + 1) * K < L ? (long long)(j + 1) * K : L) * G;
         const int R = (int)(s1 - s0);
@@ -540,8 +615,48 @@ itpp_status adjoint_w(itpp_ctx* h, int L, int K, const uint64_t* obs_x, const ui
                                                         cmap[(size_t)r], a_id + r);
             k_adj_after<<<1, 32, 0, st>>>(c2, a_cnt, a_rn, r);
         }
-        // seed of this segment's last state
         const size_t cR = cnt_log[(size_t)s1];
+        if (ev) {
+            // the recorded maps with the evaluation's weights, from the state
+            // carried into this segment (on the snapshot's order)
+            if (!chk(cudaMemcpyAsync(mu_prev, u_snap.p, c0 * 8, cudaMemcpyDeviceToDevice, st)))
+                return ITPP_ERR_CUDA;
+            for (int r = 1; r <= R; ++r) {
+                const size_t gi = (size_t)((s0 + r - 1) % G);
+                GateArg<W> g = gate_arg_of<W>(h->gates[gi]);
+                g.ch = ev->ch[gi];
+                g.msh = ev->msh[gi];
+                const size_t ci = cnt_log[(size_t)(s0 + r - 1)];
+                const size_t co = cnt_log[(size_t)(s0 + r)];
+                k_frz_step<W><<<grid, 256, 0, st>>>(rk[(size_t)r - 1], mu_prev, ci,
+                                                    rmap[(size_t)r], rmap[(size_t)r] + ci,
+                                                    rmap[(size_t)r] + 2 * ci, cmap[(size_t)r], g,
+                                                    mu_cur);
+                k_frz_trace<<<1, 32, 0, st>>>(mu_cur, a_id + r, d_tr.as<double>());
+                k_frz_scale<<<grid, 256, 0, st>>>(mu_cur, co, a_id + r, d_tr.as<double>());
+                double* t = mu_cur; mu_cur = mu_prev; mu_prev = t;
+            }
+            // mu_prev: the evaluated state on this segment's last order
+            if (j < n_seg - 1) {
+                const uint64_t cn = snap_n[(size_t)j + 1];
+                const PKey<W>* nk = snap[(size_t)j + 1].as<PKey<W>>();
+                k_adj_remap_insert<W><<<grid, 256, 0, st>>>(rk[(size_t)R], mu_prev, cR,
+                                                            static_cast<Slot<W>*>(s.table),
+                                                            s.table_slots, c2, s.probe_limit);
+                k_adj_remap_lookup<W><<<grid, 256, 0, st>>>(nk, cn, cR, u_snap.as<double>(),
+                                                            static_cast<const Slot<W>*>(s.table),
+                                                            s.table_slots, c2, s.probe_limit);
+                k_adj_bump_gen<<<1, 32, 0, st>>>(c2);
+            } else {
+                k_adj_seed<W><<<grid, 256, 0, st>>>(rk[(size_t)R], cR, d_ox, d_oz, d_wsum, d_tab,
+                                                    (int)tsize, mu_cur);
+                k_frz_dot<<<kRGrid, kRB, 0, st>>>(mu_cur, mu_prev, cR, part.as<double>());
+                k_adj_gsum<<<1, kRB, 0, st>>>(part.as<double>(), kRGrid, d_tr.as<double>(), 1);
+            }
+            if (!chk(cudaGetLastError())) return ITPP_ERR_CUDA;
+            continue;
+        }
+        // seed of this segment's last state
         if (j == n_seg - 1) {
             k_adj_seed<W><<<grid, 256, 0, st>>>(rk[(size_t)R], cR, d_ox, d_oz, d_wsum, d_tab,
                                                 (int)tsize, mu_cur);
@@ -579,6 +694,19 @@ itpp_status adjoint_w(itpp_ctx* h, int L, int K, const uint64_t* obs_x, const ui
             return ITPP_ERR_CUDA;
         if (!chk(cudaGetLastError())) return ITPP_ERR_CUDA;
     }
+    if (ev) {
+        k_adj_gen_copy<<<1, 32, 0, st>>>(s.ctl, c2);
+        double fe = 0.0;
+        int c2_status = 0;
+        if (!chk(cudaMemcpyAsync(&fe, d_tr.as<double>() + 1, 8, cudaMemcpyDeviceToHost, st)) ||
+            !chk(cudaMemcpyAsync(&c2_status, &c2->status, sizeof(int), cudaMemcpyDeviceToHost,
+                                 st)) ||
+            !chk(cudaStreamSynchronize(st)))
+            return ITPP_ERR_CUDA;
+        if (c2_status) return (itpp_status)c2_status;
+        *value = fe;
+        return ITPP_OK;
+    }
     k_adj_params<<<1, 256, 0, st>>>(gst.as<double>(), L, G, h->dtau, grad.as<double>());
     k_adj_gen_copy<<<1, 32, 0, st>>>(s.ctl, c2);
     int c2_status = 0;
@@ -614,6 +742,33 @@ extern "C" itpp_status itpp_adjoint(itpp_handle h, int n_layers, int ckpt_every,
         for (size_t j = 0; j < g_sched.size(); ++j)
             grad_alpha[h->src_gate[j]] += g_sched[j] * h->src_scale[j];
     }
+    return st;
+}
+
+extern "C" itpp_status itpp_frozen_value(itpp_handle h, int n_layers, int ckpt_every,
+                                         const double* alpha_eval, const uint64_t* obs_x,
+                                         const uint64_t* obs_z, const double* w, int m,
+                                         double* value) {
+    if (!h || n_layers < 1 || ckpt_every < 1 || !alpha_eval || !obs_x || !obs_z || !w ||
+        !value || m < 1 || m > 65536)
+        return ITPP_ERR_ARG;
+    if (h->gates.empty()) return ITPP_ERR_ARG;
+    if (h->sticky) return h->sticky;
+    FrozenEval ev;
+    ev.ch.resize(h->gates.size());
+    ev.msh.resize(h->gates.size());
+    for (size_t j = 0; j < h->gates.size(); ++j) {
+        const double a = alpha_eval[h->src_gate[j]];
+        if (!std::isfinite(a)) return ITPP_ERR_ARG;
+        const double theta = (a * h->src_scale[j]) * h->dtau;
+        ev.ch[j] = std::cosh(theta);
+        ev.msh[j] = -std::sinh(theta);
+        if (!std::isfinite(ev.ch[j]) || !std::isfinite(ev.msh[j])) return ITPP_ERR_ARG;
+    }
+    itpp_status st = h->s.W == 1
+        ? adjoint_w<1>(h, n_layers, ckpt_every, obs_x, obs_z, w, m, nullptr, value, &ev)
+        : adjoint_w<2>(h, n_layers, ckpt_every, obs_x, obs_z, w, m, nullptr, value, &ev);
+    if (st == ITPP_ERR_CUDA) h->sticky = st;
     return st;
 }
 

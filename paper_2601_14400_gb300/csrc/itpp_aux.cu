@@ -208,6 +208,7 @@ __global__ void k_import_begin(DevCtl* ctl, uint64_t count) {
         ctl->seg = 0;
         ctl->sp_lo = ctl->sp_hi = 0;
         ctl->sp_shift = 0;
+        ctl->sp_tprev = 0;
     }
 }
 
@@ -341,6 +342,7 @@ __global__ void k_reset_identity(BufsA<W> B, DevCtl* ctl) {
         ctl->seg = 0;
         ctl->sp_lo = ctl->sp_hi = 0;
         ctl->sp_shift = 0;
+        ctl->sp_tprev = 0;
         ctl->stat_gates = ctl->stat_in = ctl->stat_out = ctl->stat_cap = ctl->stat_probes = 0;
         ctl->stat_scatters = 0;
         ctl->stat_cands = 0;

@@ -6,7 +6,13 @@
 // one index space (exclusive prefix over instances), and the table-build,
 // branch-emit and top-M kernels map each item or tile back to its instance.
 // Every instance runs the device bodies of the single propagation
-// (itpp_gate_body.cuh), so its state is bit-identical to a plain run.
+// (itpp_gate_body.cuh, itpp_stage.cuh), so its state is bit-identical to a
+// plain run.  The merge (merge_path 0) is the partitioned one: every
+// instance's terms are scattered into hash partitions of the gate's pair key
+// {K, QK} (one index space of partitions over the instances), and
+// persistent CTAs merge one partition at a time in shared memory, each
+// partition's kept children claimed as one run of its instance's output;
+// merge_path 2 builds one global table per instance instead.
 // Instances with fewer gates per layer sit out the later steps.  A whole
 // layer (all steps) is captured once into a CUDA graph by the C ABI and
 // replayed, since every quantity that changes between layers lives on the
@@ -14,6 +20,7 @@
 #include "itpp_common.cuh"
 #include "itpp_gate_body.cuh"
 #include "itpp_launch.h"
+#include "itpp_stage.cuh"
 
 namespace itpp {
 
@@ -37,6 +44,13 @@ struct BatchBufs {
     unsigned long long* ccap_prefix;   // [B + 1] (compaction tiles of the select)
     uint64_t buf_cap, table_slots;
     int B, max_gates;
+    // partitioned merge
+    PKey<W>* pk;
+    double* pc;
+    unsigned int* cursor;              // [B * part_max]
+    uint64_t part_cap;
+    uint32_t part_max;
+    int part_target, merge_path;
 };
 
 template <int W>
@@ -58,7 +72,35 @@ BatchBufs<W> batch_bufs(const BatchState& s) {
     b.table_slots = s.table_slots;
     b.B = s.B;
     b.max_gates = s.max_gates;
+    b.pk = reinterpret_cast<PKey<W>*>(s.part_keys);
+    b.pc = s.part_coef;
+    b.cursor = s.part_cursor;
+    b.part_cap = s.part_cap;
+    b.part_max = s.part_max;
+    b.part_target = s.part_target;
+    b.merge_path = s.merge_path;
     return b;
+}
+
+// The pair-key partition function of a gate: the member of {K, Q.K} with
+// the gate's lowest bit clear, hashed (as the single propagation builds it
+// for a gate partitioned by its pair key).
+template <int W>
+__device__ __forceinline__ PartFn<W> pair_fn(const GateArg<W>& g) {
+    PartFn<W> f;
+    bool found = false;
+#pragma unroll
+    for (int w = 0; w < 2 * W; ++w) {
+        const uint64_t m = w < W ? g.qx[w] : g.qz[w - W];
+        const uint64_t bit = (!found && m) ? (m & (~m + 1)) : 0ULL;
+        if (w < W) f.px[w] = bit; else f.pz[w - W] = bit;
+        found = found || m;
+    }
+#pragma unroll
+    for (int w = 0; w < W; ++w) { f.kx[w] = ~0ULL; f.kz[w] = ~0ULL; }
+    f.pair = 1;
+    f.sites = 0;
+    return f;
 }
 
 // Instance owning global index i: the last b with prefix[b] <= i.
@@ -90,7 +132,12 @@ __global__ void __launch_bounds__(1024) k_b_plan(BatchBufs<W> S, int step, uint6
         const int b = base + threadIdx.x;
         unsigned long long items = 0;
         if (b < S.B && S.ctl[b].sel_pass) items = live_count(S.ctl + b, S.ctl[b].cur);
-        const unsigned long long tiles = (items + kTile - 1) / kTile;
+        // merge_path 0: tiles are the instance's pair-key partitions
+        unsigned long long tiles = (items + kTile - 1) / kTile;
+        if (S.merge_path == 0) {
+            tiles = items ? part_plan(items, S.part_cap, S.part_max, S.part_target).P : 0;
+            if (b < S.B) S.ctl[b].part_P = (uint32_t)tiles;
+        }
         unsigned long long incl = scan1024(items, s_part);
         const unsigned long long tot_i = s_part[1023];
         __syncthreads();
@@ -105,6 +152,163 @@ __global__ void __launch_bounds__(1024) k_b_plan(BatchBufs<W> S, int step, uint6
     if (threadIdx.x == 0) {
         S.item_prefix[S.B] = carry_i;
         S.tile_prefix[S.B] = carry_t;
+    }
+}
+
+// merge_path 0: every active instance's terms into the pair-key partitions
+// of its gate (one cursor claim per distinct partition per warp).
+template <int W>
+__global__ void __launch_bounds__(256) k_b_scatter(BatchBufs<W> S, int step) {
+    const unsigned long long total = S.item_prefix[S.B];
+    const unsigned int lt = (1u << (threadIdx.x & 31)) - 1u;
+    // whole warps iterate together (the claim below is warp-wide)
+    for (unsigned long long i0 = (unsigned long long)blockIdx.x * blockDim.x; i0 < total;
+         i0 += (unsigned long long)gridDim.x * blockDim.x) {
+        const unsigned long long i = i0 + threadIdx.x;
+        const bool live = i < total;
+        int b = 0;
+        uint32_t gp = 0xffffffffu, p = 0;
+        uint64_t R = 0;
+        PKey<W> K;
+        double c = 0.0;
+        if (live) {
+            b = owner(S.item_prefix, S.B, i);
+            const DevCtl* ctl = S.ctl + b;
+            const int cur = ctl->cur;
+            const uint64_t off = (uint64_t)b * S.buf_cap + (i - S.item_prefix[b]);
+            K = load_key_stream(S.k[cur] + off);
+            c = __ldcs(S.c[cur] + off);
+            const GateArg<W> g = S.gates[(size_t)b * S.max_gates + step];
+            const uint32_t P = ctl->part_P;
+            R = S.part_cap / P;
+            p = part_of(K, g, pair_fn(g), P);
+            gp = (uint32_t)b * S.part_max + p;
+        }
+        const unsigned int peers = __match_any_sync(0xffffffffu, gp);
+        const int leader = __ffs(peers) - 1;
+        unsigned int base = 0;
+        if (live && (threadIdx.x & 31) == leader) base = atomicAdd(S.cursor + gp, __popc(peers));
+        base = __shfl_sync(0xffffffffu, base, leader);
+        if (live) {
+            const unsigned int pos = base + __popc(peers & lt);
+            if (pos < R) {
+                const uint64_t d = (uint64_t)b * S.part_cap + (uint64_t)p * R + pos;
+                store_key(S.pk + d, K);
+                S.pc[d] = c;
+            } else {
+                set_status(S.ctl + b, ST_CAPACITY, 40);
+            }
+        }
+    }
+}
+
+// merge_path 0: one partition at a time per CTA (any instance), staged in
+// shared memory by two bulk copies on an mbarrier, merged by the same pass
+// as the single propagation's, its kept children one run of the instance's
+// output claimed by one atomic; partitions above the staging capacity in
+// sub-passes.  The candidate range of the single propagation's select is
+// not used (the batch's select passes over the coefficients).
+template <int W, int BLOCK>
+__global__ void __launch_bounds__(BLOCK, (BLOCK <= 256 ? 4 : 2))
+k_b_pmerge(BatchBufs<W> S, int step, double delta) {
+    using A = PassArgs<W>;
+    constexpr uint32_t C = Stage<W>::C, SL = Stage<W>::S;
+    __shared__ __align__(8) uint64_t s_bar;
+    __shared__ unsigned long long s_base;
+    __shared__ uint32_t s_n;
+    __shared__ GateArg<W> s_g;        // the partition's gate, read where used
+    __shared__ double s_rnorm;
+    if (threadIdx.x == 0) {
+        g_cn = 0u;
+        g_range[0] = g_range[1] = 0ULL;
+        mbar_init(&s_bar, 1);
+    }
+    for (uint32_t k = threadIdx.x; k < SL; k += BLOCK) A::tab()[k] = 0u;
+    __syncthreads();
+    const unsigned long long dbits = (unsigned long long)__double_as_longlong(delta);
+    const unsigned long long total = S.tile_prefix[S.B];
+    const CandRegions cd{};
+    Pending<W> pd;
+    pd.on = false;
+    pd.all_ties = false;
+    pd.T = 0;
+#pragma unroll
+    for (int w = 0; w < W; ++w) { pd.tk.x[w] = 0; pd.tk.z[w] = 0; }
+    uint32_t tag = 0, parity = 0;
+    for (unsigned long long t = blockIdx.x; t < total; t += gridDim.x) {
+        const int b = owner(S.tile_prefix, S.B, t);
+        const uint32_t p = (uint32_t)(t - S.tile_prefix[b]);
+        DevCtl* ctl = S.ctl + b;
+        const int cur = ctl->cur, nxt = cur ^ 1;
+        if (threadIdx.x == 0) {
+            s_g = S.gates[(size_t)b * S.max_gates + step];
+            s_rnorm = ctl->rnorm[cur];
+        }
+        // one read of the status for the whole CTA (and the gate published)
+        if (__syncthreads_or(threadIdx.x == 0 ? ctl->status : 0)) continue;
+        const GateArg<W>& g = s_g;
+        const double rnorm = s_rnorm;
+        const uint64_t R = S.part_cap / ctl->part_P;
+        unsigned int* cur_p = S.cursor + (uint64_t)b * S.part_max + p;
+        uint64_t np = *cur_p;
+        if (np > R) np = R;
+        const PKey<W>* kp = S.pk + (uint64_t)b * S.part_cap + (uint64_t)p * R;
+        const double* cp = S.pc + (uint64_t)b * S.part_cap + (uint64_t)p * R;
+        // selects, not a runtime index into the parameter's arrays (which
+        // would copy them to local memory)
+        PKey<W>* kout = (nxt ? S.k[1] : S.k[0]) + (uint64_t)b * S.buf_cap;
+        double* cout = (nxt ? S.c[1] : S.c[0]) + (uint64_t)b * S.buf_cap;
+        // room: one run of the instance's output, exactly the children counted
+        auto room = [&](uint32_t n_out) -> unsigned long long {
+            if (threadIdx.x == 0) {
+                unsigned long long at = n_out ? atomicAdd(&ctl->count[nxt], (unsigned long long)n_out)
+                                              : 0ULL;
+                if (at + n_out > S.buf_cap) {
+                    set_status(ctl, ST_CAPACITY, 47);
+                    at = ~0ULL;
+                }
+                s_base = at;
+            }
+            __syncthreads();
+            return s_base;
+        };
+        SelStats st{0ULL, 0u};
+        if (np <= C) {
+            const uint32_t shift = (uint32_t)((reinterpret_cast<uint64_t>(cp) >> 3) & 1ULL);
+            if (np) {
+                if (threadIdx.x == 0) {
+                    const uint32_t kb = (uint32_t)(np * sizeof(PKey<W>));
+                    const uint32_t cb = (uint32_t)(((shift + np) * sizeof(double) + 15) & ~15ULL);
+                    fence_async_shared();
+                    mbar_expect(&s_bar, kb + cb);
+                    bulk_g2s(A::keys(), kp, kb, &s_bar);
+                    bulk_g2s(A::vals(), cp - shift, cb, &s_bar);
+                }
+                const bool ok = mbar_wait(&s_bar, parity, kWaitPolls);
+                if (__syncthreads_or(!ok)) {
+                    if (threadIdx.x == 0) {
+                        set_status(ctl, ST_TIMEOUT, 45);
+                        mbar_wait(&s_bar, parity, kWaitPolls);   // the copy in flight
+                    }
+                    __syncthreads();
+                    return;
+                }
+                parity ^= 1u;
+            }
+            // every thread has read the cursor: leave it zero for the next step
+            if (threadIdx.x == 0) *cur_p = 0u;
+            tag = next_tag<W, BLOCK>(tag, A::tab());
+            stage_pass<W, BLOCK>((uint32_t)np, shift, g, pd, rnorm, dbits, ctl, nxt, tag, kout,
+                                 cout, st, cd, room);
+        } else {
+            merge_long<W, BLOCK>(kp, cp, np, g, pd, rnorm, dbits, ctl, nxt, &tag, kout, cout, st,
+                                 cd, ~0ULL, room, cur_p, &s_n);
+        }
+        // the largest written pattern (overflow check of post_one)
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1)
+            st.out_max = max(st.out_max, __shfl_xor_sync(0xffffffffu, st.out_max, o));
+        if ((threadIdx.x & 31) == 0 && st.out_max) atomicMax(&ctl->out_max, st.out_max);
     }
 }
 
@@ -334,17 +538,55 @@ __global__ void k_b_cap_end(BatchBufs<W> S) {
 // ---------------------------------------------------------------------------
 // Launchers
 // ---------------------------------------------------------------------------
+// CTAs per SM of the partition merge that fit (shared memory, registers),
+// with its dynamic shared memory allowed; called before any capture.
+template <int W, int BLOCK>
+static int pmerge_fit() {
+    constexpr size_t smem = Stage<W>::kBytes;
+    cudaFuncSetAttribute(k_b_pmerge<W, BLOCK>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)smem);
+    cudaFuncSetAttribute(k_b_pmerge<W, BLOCK>, cudaFuncAttributePreferredSharedMemoryCarveout,
+                         (int)cudaSharedmemCarveoutMaxShared);
+    int per_sm = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_b_pmerge<W, BLOCK>, BLOCK, smem);
+    return per_sm > 0 ? per_sm : 1;
+}
+
+template <int W>
+static int pmerge_fit_w(int block) {
+    switch (block) {
+        case 128: return pmerge_fit<W, 128>();
+        case 512: return pmerge_fit<W, 512>();
+        default: return pmerge_fit<W, 256>();
+    }
+}
+
+int batch_merge_fit(int W, int block) {
+    return W == 1 ? pmerge_fit_w<1>(block) : pmerge_fit_w<2>(block);
+}
+
 template <int W>
 static cudaError_t batch_step_w(const BatchState& s, int step, cudaStream_t st) {
     const BatchBufs<W> S = batch_bufs<W>(s);
     const int grid = s.num_sms * 8;
     k_b_plan<W><<<1, 1024, 0, st>>>(S, step, (uint64_t)s.main_block * kIpt);
-    k_b_insert<W><<<s.num_sms * s.insert_grid, 256, 0, st>>>(S, step, s.load_pct, s.probe_limit);
-    const int gm = s.num_sms * s.main_grid;
-    switch (s.main_block) {
-        case 128: k_b_main<W, 128><<<gm, 128, 0, st>>>(S, step, s.delta, s.load_pct, s.probe_limit); break;
-        case 512: k_b_main<W, 512><<<gm, 512, 0, st>>>(S, step, s.delta, s.load_pct, s.probe_limit); break;
-        default:  k_b_main<W, 256><<<gm, 256, 0, st>>>(S, step, s.delta, s.load_pct, s.probe_limit); break;
+    if (s.merge_path == 0) {
+        k_b_scatter<W><<<s.num_sms * s.scatter_grid, 256, 0, st>>>(S, step);
+        const int gm = s.num_sms * s.merge_ctas;
+        constexpr size_t smem = Stage<W>::kBytes;
+        switch (s.main_block) {
+            case 128: k_b_pmerge<W, 128><<<gm, 128, smem, st>>>(S, step, s.delta); break;
+            case 512: k_b_pmerge<W, 512><<<gm, 512, smem, st>>>(S, step, s.delta); break;
+            default:  k_b_pmerge<W, 256><<<gm, 256, smem, st>>>(S, step, s.delta); break;
+        }
+    } else {
+        k_b_insert<W><<<s.num_sms * s.insert_grid, 256, 0, st>>>(S, step, s.load_pct, s.probe_limit);
+        const int gm = s.num_sms * s.main_grid;
+        switch (s.main_block) {
+            case 128: k_b_main<W, 128><<<gm, 128, 0, st>>>(S, step, s.delta, s.load_pct, s.probe_limit); break;
+            case 512: k_b_main<W, 512><<<gm, 512, 0, st>>>(S, step, s.delta, s.load_pct, s.probe_limit); break;
+            default:  k_b_main<W, 256><<<gm, 256, 0, st>>>(S, step, s.delta, s.load_pct, s.probe_limit); break;
+        }
     }
     k_b_post<W><<<1, 1024, 0, st>>>(S, s.cap_M, s.cap_policy);
     if (s.cap_policy == 1) {

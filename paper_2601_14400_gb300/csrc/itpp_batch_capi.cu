@@ -26,11 +26,13 @@ struct itpp_batch_ctx {
     uint64_t launches = 0;
     std::vector<unsigned char> h_ctl;   // one DevCtl head, for reads
     int load_floor = 50;                // lowest table load the allocation allows
+    bool target_fixed = false;          // partition size given by the caller
 };
 
 namespace {
 
 constexpr size_t kHead = offsetof(DevCtl, sel_hist);
+constexpr int kTargetMin = 150;   // smallest mean partition size the autotuner tries
 
 uint64_t next_pow2(uint64_t v) {
     uint64_t s = 1;
@@ -55,6 +57,9 @@ void free_batch(itpp_batch_ctx* h) {
         if (s.coef[i]) cudaFree(s.coef[i]);
     }
     if (s.table) cudaFree(s.table);
+    if (s.part_keys) cudaFree(s.part_keys);
+    if (s.part_coef) cudaFree(s.part_coef);
+    if (s.part_cursor) cudaFree(s.part_cursor);
     if (s.ctls) cudaFree(s.ctls);
     if (s.gates) cudaFree(s.gates);
     if (s.n_gates) cudaFree(s.n_gates);
@@ -118,11 +123,24 @@ itpp_status read_head(itpp_batch_ctx* h, int b, DevCtl* out) {
     return ITPP_OK;
 }
 
-// Reset every instance to the identity (statistics cleared).
+// Reset every instance to the identity (statistics cleared, partition
+// cursors zero).
 itpp_status reset_all(itpp_batch_ctx* h) {
-    for (int b = 0; b < h->s.B; ++b)
+    const BatchState& s = h->s;
+    if (s.part_cursor &&
+        cudaMemsetAsync(s.part_cursor, 0, (size_t)s.B * s.part_max * sizeof(unsigned int),
+                        h->stream) != cudaSuccess)
+        return ITPP_ERR_CUDA;
+    for (int b = 0; b < s.B; ++b)
         if (launch_reset_identity(view(h, b), h->stream) != cudaSuccess) return ITPP_ERR_CUDA;
     return ITPP_OK;
+}
+
+// The partition merge's CTAs per SM: the requested count, at most what fits
+// at the current block size (0: what fits).
+void fit_merge(BatchState& s, int want) {
+    const int fit = batch_merge_fit(s.W, s.main_block);
+    s.merge_ctas = (want > 0 && want < fit) ? want : fit;
 }
 
 // Capture one Trotter layer (every gate step, all instances per launch) as
@@ -183,7 +201,9 @@ itpp_status itpp_batch_create(int B, const int* n, const int* n_gates, const uin
     if (!std::isfinite(dtau) || !(p->delta >= 0.0) || !std::isfinite(p->delta)) return ITPP_ERR_ARG;
     if (p->cap_M < 1 || p->cap_M > (1ULL << 31)) return ITPP_ERR_ARG;
     if (p->cap_policy != 0 && p->cap_policy != 1) return ITPP_ERR_ARG;
-    if (p->merge_path != 0) return ITPP_ERR_ARG;
+    if (p->merge_path != 0 && p->merge_path != 2) return ITPP_ERR_ARG;
+    if (p->partition_target != 0 && (p->partition_target < 64 || p->partition_target > 2048))
+        return ITPP_ERR_ARG;
     if (p->max_weight < 0 || p->max_weight > 128) return ITPP_ERR_ARG;
     int max_n = 0, max_g = 0;
     long long total_g = 0;
@@ -226,9 +246,21 @@ itpp_status itpp_batch_create(int B, const int* n, const int* n_gates, const uin
     s.cap_M = p->cap_M;
     s.buf_cap = 2 * p->cap_M;
     s.cap_policy = p->cap_policy;
+    s.merge_path = p->merge_path;
     s.delta = p->delta + 0.0;   // -0 becomes +0 (the threshold compares bit patterns)
     s.load_pct = p->table_load_pct ? p->table_load_pct : 50;
     if (s.load_pct < 10 || s.load_pct > 75) { free_batch(h); delete h; return ITPP_ERR_ARG; }
+    if (s.merge_path == 0) {
+        // scatter buffer per instance (even: a staging copy may start one
+        // element below an odd partition start); cursors for the smallest
+        // partition size the autotuner tries
+        h->target_fixed = p->partition_target != 0;
+        s.part_target = p->partition_target ? p->partition_target : partition_target_default(W);
+        s.part_cap = 2 * p->cap_M + p->cap_M / 2 + 4096;
+        s.part_cap += s.part_cap & 1ULL;
+        const int t_min = h->target_fixed ? s.part_target : kTargetMin;
+        s.part_max = partition_max(p->cap_M, t_min < s.part_target ? t_min : s.part_target);
+    }
     // auto sizing leaves room for the autotuner to try loads down to 25 %
     const int load_for_size = p->table_load_pct ? (s.load_pct < 50 ? s.load_pct : 50) : 25;
     h->load_floor = load_for_size;
@@ -258,6 +290,13 @@ itpp_status itpp_batch_create(int B, const int* n, const int* n_gates, const uin
                         cudaSuccess;
     }
     ok &= ok && cudaMalloc(&s.table, (size_t)B * s.table_slots * slot) == cudaSuccess;
+    if (s.merge_path == 0) {
+        ok &= ok && cudaMalloc(&s.part_keys, (size_t)B * s.part_cap * 16 * W) == cudaSuccess;
+        ok &= ok && cudaMalloc(reinterpret_cast<void**>(&s.part_coef),
+                               ((size_t)B * s.part_cap + 2) * 8) == cudaSuccess;
+        ok &= ok && cudaMalloc(reinterpret_cast<void**>(&s.part_cursor),
+                               (size_t)B * s.part_max * sizeof(unsigned int)) == cudaSuccess;
+    }
     ok &= ok && cudaMalloc(reinterpret_cast<void**>(&s.ctls), (size_t)B * sizeof(DevCtl)) == cudaSuccess;
     ok &= ok && cudaMalloc(&s.gates, gates.size()) == cudaSuccess;
     ok &= ok && cudaMalloc(reinterpret_cast<void**>(&s.n_gates), (size_t)B * sizeof(int)) == cudaSuccess;
@@ -277,6 +316,11 @@ itpp_status itpp_batch_create(int B, const int* n, const int* n_gates, const uin
     ok &= cudaMemsetAsync(s.table, 0, (size_t)B * s.table_slots * slot, h->stream) == cudaSuccess;
     ok &= cudaMemsetAsync(s.ctls, 0, (size_t)B * sizeof(DevCtl), h->stream) == cudaSuccess;
     ok &= cudaMemsetAsync(s.item_prefix, 0, 4 * (size_t)(B + 1) * sizeof(unsigned long long), h->stream) == cudaSuccess;
+    if (s.merge_path == 0) {
+        ok &= cudaMemsetAsync(s.part_cursor, 0, (size_t)B * s.part_max * sizeof(unsigned int),
+                              h->stream) == cudaSuccess;
+        fit_merge(s, 0);
+    }
     for (int b = 0; b < B && ok; ++b) {
         DeviceState d = view(h, b);
         ok &= cudaMemcpyAsync(&d.ctl->buf_cap, &s.buf_cap, sizeof(s.buf_cap),
@@ -318,9 +362,26 @@ itpp_status itpp_batch_autotune(itpp_batch_handle h, int probe_layers, itpp_tune
     if (!h || probe_layers < 1) return ITPP_ERR_ARG;
     if (h->sticky) return h->sticky;
     BatchState& s = h->s;
-    struct Shape { int mb, mg, ig, load; };
-    Shape best{256, 4, 8, 50 < h->load_floor ? h->load_floor : 50};
-    s.main_block = best.mb; s.main_grid = best.mg; s.insert_grid = best.ig; s.load_pct = best.load;
+    const bool part = s.merge_path == 0;
+    // a shape: block, CTAs per SM of the merge (partitioned: 0 = what fits)
+    // or of the branch-emit kernel, CTAs per SM of the scatter or table
+    // build, table load (global table) or mean partition size (partitioned)
+    struct Shape { int mb, mg, ig, load, target; };
+    auto install = [&](const Shape& c) {
+        s.main_block = c.mb;
+        if (part) {
+            fit_merge(s, c.mg);
+            s.scatter_grid = c.ig;
+            s.part_target = c.target;
+        } else {
+            s.main_grid = c.mg;
+            s.insert_grid = c.ig;
+            s.load_pct = c.load;
+        }
+    };
+    Shape best = part ? Shape{256, 0, 8, 0, s.part_target}
+                      : Shape{256, 4, 8, 50 < h->load_floor ? h->load_floor : 50, 0};
+    install(best);
     double best_ms = 0, default_ms = 0;
     int tried = 0;
     itpp_status st = time_shape(h, probe_layers, &best_ms);
@@ -328,7 +389,7 @@ itpp_status itpp_batch_autotune(itpp_batch_handle h, int probe_layers, itpp_tune
     default_ms = best_ms;
     ++tried;
     auto try_shape = [&](Shape c) -> itpp_status {
-        s.main_block = c.mb; s.main_grid = c.mg; s.insert_grid = c.ig; s.load_pct = c.load;
+        install(c);
         double ms = 0;
         itpp_status e = time_shape(h, probe_layers, &ms);
         if (e) return e;
@@ -337,14 +398,28 @@ itpp_status itpp_batch_autotune(itpp_batch_handle h, int probe_layers, itpp_tune
         return ITPP_OK;
     };
     // one parameter at a time, each from the best shape so far
-    const int blocks[3] = {128, 256, 512}, grids[3] = {2, 4, 8}, igrids[3] = {4, 8, 16};
-    const int loads[4] = {25, 35, 50, 65};
+    const int blocks[3] = {128, 256, 512};
     for (int v : blocks) if (v != best.mb) { Shape c = best; c.mb = v; if ((st = try_shape(c))) return h->sticky = st; }
-    for (int v : grids) if (v != best.mg) { Shape c = best; c.mg = v; if ((st = try_shape(c))) return h->sticky = st; }
-    for (int v : igrids) if (v != best.ig) { Shape c = best; c.ig = v; if ((st = try_shape(c))) return h->sticky = st; }
-    for (int v : loads)
-        if (v != best.load && v >= h->load_floor) { Shape c = best; c.load = v; if ((st = try_shape(c))) return h->sticky = st; }
-    s.main_block = best.mb; s.main_grid = best.mg; s.insert_grid = best.ig; s.load_pct = best.load;
+    if (part) {
+        const int mgs[3] = {2, 4, 0}, sgs[3] = {4, 8, 16};
+        const int t1[4] = {350, 500, 700, 1000}, t2[3] = {150, 300, 450};
+        for (int v : mgs) if (v != best.mg) { Shape c = best; c.mg = v; if ((st = try_shape(c))) return h->sticky = st; }
+        for (int v : sgs) if (v != best.ig) { Shape c = best; c.ig = v; if ((st = try_shape(c))) return h->sticky = st; }
+        if (!h->target_fixed) {
+            const int* ts = s.W == 1 ? t1 : t2;
+            const int nt = s.W == 1 ? 4 : 3;
+            for (int k = 0; k < nt; ++k)
+                if (ts[k] != best.target) { Shape c = best; c.target = ts[k]; if ((st = try_shape(c))) return h->sticky = st; }
+        }
+    } else {
+        const int grids[3] = {2, 4, 8}, igrids[3] = {4, 8, 16};
+        const int loads[4] = {25, 35, 50, 65};
+        for (int v : grids) if (v != best.mg) { Shape c = best; c.mg = v; if ((st = try_shape(c))) return h->sticky = st; }
+        for (int v : igrids) if (v != best.ig) { Shape c = best; c.ig = v; if ((st = try_shape(c))) return h->sticky = st; }
+        for (int v : loads)
+            if (v != best.load && v >= h->load_floor) { Shape c = best; c.load = v; if ((st = try_shape(c))) return h->sticky = st; }
+    }
+    install(best);
     if (h->layer) {
         cudaGraphExecDestroy(h->layer);
         h->layer = nullptr;
@@ -356,9 +431,10 @@ itpp_status itpp_batch_autotune(itpp_batch_handle h, int probe_layers, itpp_tune
     if (out) {
         std::memset(out, 0, sizeof(*out));
         out->main_block = best.mb;
-        out->main_grid = best.mg;
+        out->main_grid = part ? s.merge_ctas : best.mg;
         out->insert_grid = best.ig;
-        out->table_load_pct = best.load;
+        out->table_load_pct = part ? 0 : best.load;
+        out->partition_target = part ? best.target : 0;
         out->ms_per_probe = best_ms;
         out->ms_per_probe_default = default_ms;
         out->candidates = tried;

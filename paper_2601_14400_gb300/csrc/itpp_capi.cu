@@ -66,6 +66,7 @@ void free_all(itpp_ctx* h) {
     if (h->sort_mem) cudaFree(h->sort_mem);
     if (h->psd_mem) cudaFree(h->psd_mem);
     if (h->s.cand.cnt) cudaFree(h->s.cand.cnt);
+    if (h->s.sp_drift) cudaFree(h->s.sp_drift);
     if (h->h_ctl) cudaFreeHost(h->h_ctl);
     for (int k = 0; k < kKinds; ++k)
         for (auto& e : h->ev[k]) { cudaEventDestroy(e.a); cudaEventDestroy(e.b); }
@@ -153,7 +154,7 @@ itpp_status launch_one_gate(itpp_ctx* h, int k) {
     h->launches += 3;
     if (e == cudaSuccess && h->s.cap_policy == 1) {
         EventPair* ev2 = prof_begin(h, 2);
-        e = launch_cap(h->s, h->stream);
+        e = launch_cap(h->s, h->stream, k);
         prof_end(h, ev2);
         h->launches += cap_launches(h->s);
     }
@@ -433,7 +434,13 @@ itpp_status itpp_create(int n, const uint64_t* gate_x, const uint64_t* gate_z,
             s.cand.idx = reinterpret_cast<uint32_t*>(s.cand.v + ent);
             s.cand.region = region;
         }
-        s.cand_hi = std::max<uint64_t>(4096, std::min<uint64_t>(p->cap_M / 16, ent / 8));
+        // the candidate range narrows while the merge lists more than this
+        s.cand_hi = std::max<uint64_t>(16384, std::min<uint64_t>(p->cap_M / 16, ent / 8));
+        s.layer_gates = (int)h->gates.size();
+        ok &= ok && cudaMalloc(reinterpret_cast<void**>(&s.sp_drift),
+                               (size_t)(s.layer_gates + 1) * sizeof(long long)) == cudaSuccess;
+        ok &= ok && cudaMemsetAsync(s.sp_drift, 0, (size_t)(s.layer_gates + 1) * sizeof(long long),
+                                    h->stream) == cudaSuccess;
         plan_windows(W, h->gates);
     }
     if (ok && p->merge_path == 1) {

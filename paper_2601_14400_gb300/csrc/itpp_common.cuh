@@ -116,6 +116,7 @@ struct DevCtl {
     // the previous gate's threshold); the select then reads only that list
     unsigned long long sp_lo, sp_hi; // candidate range (sp_hi == 0: none)
     unsigned long long sp_above;     // kept children with pattern > sp_hi
+    unsigned long long sp_tprev;     // the last select's threshold pattern (0: none)
     int sp_ovf;                      // a CTA's candidate region overflowed
     int sp_shift;                    // log2 of the range's half-width (0: unset)
     unsigned int cand_regions;       // regions of the candidate list in use

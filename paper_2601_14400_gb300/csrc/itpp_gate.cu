@@ -419,8 +419,8 @@ cudaError_t launch_materialize(const DeviceState& s, cudaStream_t st) {
     return s.W == 1 ? materialize_w<1>(s, st) : materialize_w<2>(s, st);
 }
 
-cudaError_t launch_cap(const DeviceState& s, cudaStream_t st) {
-    if (s.merge_deferred) return launch_select_deferred(s, st);
+cudaError_t launch_cap(const DeviceState& s, cudaStream_t st, int gate) {
+    if (s.merge_deferred) return launch_select_deferred(s, st, gate);
     return s.W == 1 ? cap_w<1>(s, st) : cap_w<2>(s, st);
 }
 

@@ -65,6 +65,10 @@ struct DeviceState {
     int max_ctas = 0;                 // CTAs of the merge and select grids at most
     CandRegions cand;                 // one allocation: cnt[max_ctas], then v, then idx
     uint64_t cand_hi = 0;             // candidate count above which the range narrows
+    // per gate of a layer: how the select's threshold pattern moved at that
+    // gate (the prediction of the next layer's), and the number of gates
+    long long* sp_drift = nullptr;
+    int layer_gates = 0;
     // top-M select leaves its kept set as a predicate for the next scatter
     bool merge_deferred = false;
 };
@@ -105,14 +109,16 @@ uint64_t merge_slack(uint64_t cap_M, int max_ctas);
 // window fields of every gate).
 void plan_windows(int W, std::vector<HostGate>& gates);
 // Top-M select and compaction (no-ops on the device when the bound holds).
-cudaError_t launch_cap(const DeviceState& s, cudaStream_t st);
+// gate: the gate's index in the layer's schedule (the partitioned merge's
+// select predicts the next threshold from the same gate of the last layer).
+cudaError_t launch_cap(const DeviceState& s, cudaStream_t st, int gate = 0);
 int cap_launches(const DeviceState& s);
 // The select part only (threshold and tie key in the control block, no
 // compaction): used where the kept set is compacted elsewhere.
 cudaError_t launch_cap_select(const DeviceState& s, cudaStream_t st);
 // The top-M select of the partitioned merge (itpp_select.cu): leaves the
 // kept set as a predicate for the next gate's reads.
-cudaError_t launch_select_deferred(const DeviceState& s, cudaStream_t st);
+cudaError_t launch_select_deferred(const DeviceState& s, cudaStream_t st, int gate);
 int select_deferred_launches(int W);
 // Apply a deferred top-M select and gather a segmented state into one
 // contiguous run (compaction); a no-op when neither is there.
@@ -166,10 +172,25 @@ struct BatchState {
     // launch shape (autotuned): branch-emit block (x2 items per thread), grid
     // multipliers (CTAs per SM) of the branch-emit and table-build kernels
     int main_block = 256, main_grid = 4, insert_grid = 8;
+    // merge_path 0 (partitioned merge): per instance a scatter buffer of
+    // part_cap terms in at most part_max pair-key partitions; the merge's
+    // CTAs per SM (0: as many as fit) and the scatter's, and the mean
+    // partition size (autotuned); merge_path 2: the global table above
+    int merge_path = 0;
+    void* part_keys = nullptr;                    // [B * part_cap] keys
+    double* part_coef = nullptr;                  // [B * part_cap + 2]
+    unsigned int* part_cursor = nullptr;          // [B * part_max]
+    uint64_t part_cap = 0;
+    uint32_t part_max = 0;
+    int part_target = 0, merge_ctas = 0, scatter_grid = 8;
 };
 
 // Gate `step` of the layer for every instance that has one.
 cudaError_t launch_batch_step(const BatchState& s, int step, cudaStream_t st);
+// CTAs per SM of the batch's partition merge that fit, for W mask words and
+// `block` threads per CTA (sets the kernel's shared-memory attributes: call
+// it before capturing a layer).
+int batch_merge_fit(int W, int block);
 int batch_step_launches(const BatchState& s);
 
 }  // namespace itpp

@@ -30,198 +30,9 @@
 #include "itpp_common.cuh"
 #include "itpp_gate_body.cuh"
 #include "itpp_launch.h"
+#include "itpp_stage.cuh"
 
 namespace itpp {
-
-namespace {
-
-
-// Partition geometry per word count: the mean partition size the scatter
-// aims for, and the largest window (sites; a group holds at most 4^sites
-// terms).
-template <int W> struct PartGeom;
-template <> struct PartGeom<1> {
-    static constexpr int kTarget = 700, kWinSites = 5;
-};
-template <> struct PartGeom<2> {
-    static constexpr int kTarget = 300, kWinSites = 4;
-};
-
-struct PartPlan {
-    uint32_t P;     // partitions
-    uint64_t R;     // stride (capacity) of one partition in the scatter buffer
-};
-
-__device__ __forceinline__ PartPlan part_plan(uint64_t n, uint64_t pbuf_cap, uint32_t p_max,
-                                              int target) {
-    uint64_t P = (n + target - 1) / target;
-    if (P < 1) P = 1;
-    if (P > p_max) P = p_max;
-    PartPlan pl;
-    pl.P = (uint32_t)P;
-    pl.R = pbuf_cap / P;
-    return pl;
-}
-
-// The partition function of a window: the hash of the key with the
-// window's sites cleared, or (pair mode) of the gate's pair key.
-template <int W>
-struct PartFn {
-    uint64_t kx[W], kz[W];   // bits kept by the mask
-    int pair;                // 1: pair-key mode
-    int sites;               // sites of the window (mask mode)
-    uint64_t px[W], pz[W];   // the pivot: the gate's lowest bit (all zero for Q = I)
-};
-
-// Mask mode needs many more possible groups than terms: a group (the terms
-// with one pattern outside the window) holds up to 4^sites of them, and a
-// partition that collects several large groups could outgrow its stride or
-// the shared table.  So the window's mask is used only while
-// 4^(n - sites) >= 64 N; a denser state (a small or saturated chain) falls
-// back to the pair key of the window's first gate, valid for that gate only.
-__device__ __forceinline__ bool window_fits(int n_sites, int w_sites, uint64_t n_terms) {
-    const int free_bits = 2 * (n_sites - w_sites);
-    const int need_bits = 6 + (n_terms > 1 ? 64 - __clzll((long long)(n_terms - 1)) : 0);
-    return free_bits >= need_bits;
-}
-
-template <int W>
-__device__ __forceinline__ uint32_t part_of(const PKey<W>& K, const GateArg<W>& g,
-                                            const PartFn<W>& f, uint32_t P) {
-    // masks and element-wise selects only: a conditional copy of the key,
-    // or a selection of one of its words by index, puts the caller's key
-    // arrays in local memory
-    uint64_t piv = 0;
-#pragma unroll
-    for (int v = 0; v < W; ++v) piv |= (K.x[v] & f.px[v]) | (K.z[v] & f.pz[v]);
-    const uint64_t flip = piv ? ~0ULL : 0ULL;   // pivot set: the pair key is K.Q
-    PKey<W> k;
-    if (f.pair) {   // the pair key K.Q when the pivot is set
-#pragma unroll
-        for (int v = 0; v < W; ++v) { k.x[v] = K.x[v] ^ (g.qx[v] & flip); k.z[v] = K.z[v] ^ (g.qz[v] & flip); }
-    } else {        // the key with the window's sites cleared
-#pragma unroll
-        for (int v = 0; v < W; ++v) { k.x[v] = K.x[v] & f.kx[v]; k.z[v] = K.z[v] & f.kz[v]; }
-    }
-    const uint64_t h = key_hash(k);   // 32 significant bits
-    return (uint32_t)((h * (uint64_t)P) >> 32);
-}
-
-// The kept set of a deferred top-M select, applied where terms are read.
-template <int W>
-struct Pending {
-    bool on, all_ties;
-    unsigned long long T;
-    PKey<W> tk;
-};
-
-template <int W>
-__device__ __forceinline__ Pending<W> pending_of(const DevCtl* ctl) {
-    Pending<W> q;
-    q.on = ctl->pend != 0;
-    q.all_ties = ctl->pend_all_ties != 0;
-    q.T = ctl->pend_T;
-#pragma unroll
-    for (int w = 0; w < W; ++w) { q.tk.x[w] = ctl->pend_tie_key[w]; q.tk.z[w] = ctl->pend_tie_key[W + w]; }
-    return q;
-}
-
-// Prefetch [p, p + bytes) into L2 with one bulk (TMA) request; the range is
-// widened to 16-byte boundaries, which every buffer it is used on allows
-// (its byte size is a multiple of 16).
-__device__ __forceinline__ void l2_prefetch_bulk(const void* p, uint64_t bytes) {
-    const uint64_t a = reinterpret_cast<uint64_t>(p);
-    const uint64_t lo = a & ~15ULL;
-    uint64_t sz = ((a + bytes + 15ULL) & ~15ULL) - lo;
-    if (sz > (1ULL << 20)) sz = 1ULL << 20;
-    if (sz) asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" :: "l"(lo), "r"((uint32_t)sz)
-                         : "memory");
-}
-
-// ---------------------------------------------------------------------------
-// Bulk (TMA) copies into shared memory, completed on an mbarrier.  A copy
-// needs 16-byte aligned addresses and a size that is a multiple of 16 bytes.
-// ---------------------------------------------------------------------------
-__device__ __forceinline__ uint32_t smem_addr(const void* p) {
-    return (uint32_t)__cvta_generic_to_shared(p);
-}
-
-__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" :: "r"(smem_addr(bar)), "r"(count)
-                 : "memory");
-    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-}
-
-// Arrive on the barrier and announce `bytes` of copies that complete it.
-__device__ __forceinline__ void mbar_expect(uint64_t* bar, uint32_t bytes) {
-    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;"
-                 :: "r"(smem_addr(bar)), "r"(bytes) : "memory");
-}
-
-__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t bytes,
-                                         uint64_t* bar) {
-    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes "
-                 "[%0], [%1], %2, [%3];"
-                 :: "r"(smem_addr(dst)), "l"(src), "r"(bytes), "r"(smem_addr(bar)) : "memory");
-}
-
-// Generic-proxy accesses to shared memory made before this fence are ordered
-// before later bulk copies into it.
-__device__ __forceinline__ void fence_async_shared() {
-    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-}
-
-// Wait for the barrier's phase `parity` to complete, at most `limit` polls
-// (each poll may itself suspend the thread for a while).  False: timed out.
-__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, uint32_t limit) {
-    const uint32_t a = smem_addr(bar);
-    for (uint32_t it = 0; it < limit; ++it) {
-        uint32_t done;
-        // the thread sleeps in the wait until the phase completes or the
-        // hint (nanoseconds) runs out, instead of polling
-        asm volatile("{\n\t.reg .pred p;\n\t"
-                     "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n\t"
-                     "selp.u32 %0, 1, 0, p;\n\t}"
-                     : "=r"(done) : "r"(a), "r"(parity), "r"(1000000u) : "memory");
-        if (done) return true;
-    }
-    return false;
-}
-
-// Sub-pass of a long partition's commuting string: a hash of the key with
-// the gate's sites cleared, which K and Q.K share (they differ exactly on
-// Q's bits), so a string and its partner always fall into the same one.
-template <int W>
-__device__ __forceinline__ uint32_t sub_pass(const PKey<W>& K, const GateArg<W>& g, uint32_t k) {
-    PKey<W> m;
-#pragma unroll
-    for (int w = 0; w < W; ++w) { m.x[w] = K.x[w] & ~g.qx[w]; m.z[w] = K.z[w] & ~g.qz[w]; }
-    return (uint32_t)((key_hash(m) * (uint64_t)k) >> 32);
-}
-
-// Append one value per lane that has one (every lane of the warp calls it)
-// to this CTA's region of the candidate list: one shared-memory atomic per
-// warp; entries past the region's end are dropped and counted, and the
-// select then falls back to its full passes.
-__device__ __forceinline__ void cand_push(bool hit, unsigned long long v, uint64_t pos,
-                                          const CandRegions& cd, uint32_t* s_cn) {
-    const unsigned int m = __ballot_sync(0xffffffffu, hit);
-    if (!m) return;
-    const int lane = threadIdx.x & 31, leader = __ffs(m) - 1;
-    uint32_t q = 0;
-    if (lane == leader) q = atomicAdd(s_cn, (uint32_t)__popc(m));
-    q = __shfl_sync(0xffffffffu, q, leader);
-    if (hit) {
-        const uint64_t r = (uint64_t)q + __popc(m & ((1u << lane) - 1u));
-        if (r < cd.region) {
-            const uint64_t e = (uint64_t)blockIdx.x * cd.region + r;
-            cd.v[e] = v;
-            cd.idx[e] = (uint32_t)pos;
-        }
-    }
-}
-
-}  // namespace
 
 // Scatter the current state into the partitions of a window (force), or,
 // inside a window, only when the previous gate's partitions hold for that
@@ -334,271 +145,6 @@ k_part_scatter(Bufs<W> B, DevCtl* ctl, PKey<W>* pk, double* pc, unsigned int* cu
     }
 }
 
-// Items a CTA stages in shared memory for one pass, and the slots of its
-// pair table (at most half full).
-template <int W> struct StageGeom;
-template <> struct StageGeom<1> { static constexpr int kItems = 1024, kSlots = 2048; };
-template <> struct StageGeom<2> { static constexpr int kItems = 512, kSlots = 1024; };
-
-// Dynamic shared memory of the merge: the staged keys, their values (raw
-// coefficient in, normalised coefficient after phase A, merged child after
-// phase B; two spare slots let a copy start at the 16-byte boundary below an
-// odd element), the partner children b, the pair table and per-item flags.
-template <int W>
-struct Stage {
-    static constexpr int C = StageGeom<W>::kItems, S = StageGeom<W>::kSlots;
-    static constexpr size_t kKeys = 0;
-    static constexpr size_t kVals = kKeys + sizeof(PKey<W>) * C;
-    static constexpr size_t kB = kVals + sizeof(double) * (C + 2);
-    static constexpr size_t kTab = kB + sizeof(double) * C;
-    static constexpr size_t kFlags = kTab + sizeof(uint32_t) * S;
-    static constexpr size_t kBytes = (kFlags + C + 15) / 16 * 16;
-    static_assert(kVals % 16 == 0 && kB % 16 == 0 && kTab % 16 == 0, "alignment");
-};
-
-// Waits on a staging copy's barrier before the CTA gives up: each wait
-// sleeps up to a millisecond, and a copy of a few tens of kilobytes completes
-// within microseconds; this bound is seconds.
-constexpr uint32_t kWaitPolls = 4096u;
-
-// Slot of a key in a CTA's pair table: a multiply-xor of the key's 32-bit
-// halves and one xorshift-multiply round.  Partitions are chosen by the full
-// hash of a different key (masked or pair key), so the two are independent.
-template <int W>
-__device__ __forceinline__ uint32_t slot_hash(const PKey<W>& k) {
-    constexpr uint32_t C[8] = {0x9E3779B1u, 0x85EBCA77u, 0xC2B2AE3Du, 0x27D4EB2Fu,
-                               0x165667B1u, 0xD3A2646Du, 0xFD7046C5u, 0xB55A4F09u};
-    uint32_t h = 0;
-#pragma unroll
-    for (int w = 0; w < W; ++w) {
-        h ^= (uint32_t)k.x[w] * C[4 * w] ^ (uint32_t)(k.x[w] >> 32) * C[4 * w + 1];
-        h ^= (uint32_t)k.z[w] * C[4 * w + 2] ^ (uint32_t)(k.z[w] >> 32) * C[4 * w + 3];
-    }
-    h ^= h >> 15;
-    h *= 0x2C1B3C6Du;
-    h ^= h >> 12;
-    return h;
-}
-
-// Pair table of one pass: slot = (tag << 16) | index of a staged commuting
-// string.  Tags grow with every pass of the CTA, so a slot of an earlier
-// pass is free and the table needs no clearing.
-template <int W>
-__device__ __forceinline__ bool pair_insert(const PKey<W>& K, uint32_t i, uint32_t* tab,
-                                            uint32_t tag) {
-    constexpr uint32_t S = StageGeom<W>::kSlots;
-    const uint32_t mine = (tag << 16) | i;
-    uint32_t h = slot_hash(K) & (S - 1);
-    for (uint32_t q = 0; q < S; ++q) {
-        uint32_t v = tab[h];
-        while ((v >> 16) != tag) {          // free: claim it
-            const uint32_t o = atomicCAS(tab + h, v, mine);
-            if (o == v) return true;
-            v = o;
-        }
-        h = (h + 1) & (S - 1);
-    }
-    return false;
-}
-
-template <int W>
-__device__ __forceinline__ bool pair_find(const PKey<W>& P, const PKey<W>* keys_s,
-                                          const double* b_s, const uint32_t* tab, uint32_t tag,
-                                          double* out) {
-    constexpr uint32_t S = StageGeom<W>::kSlots;
-    uint32_t h = slot_hash(P) & (S - 1);
-    for (uint32_t q = 0; q < S; ++q) {
-        const uint32_t v = tab[h];
-        if ((v >> 16) != tag) return false;
-        const uint32_t j = v & 0xffffu;
-        if (key_eq(keys_s[j], P)) { *out = b_s[j]; return true; }
-        h = (h + 1) & (S - 1);
-    }
-    return false;
-}
-
-// Exclusive block scan with one barrier: every warp writes its total, then
-// every warp scans the warp totals with shuffles (s_warp may be rewritten
-// only after the caller's next barrier).
-template <int BLOCK>
-__device__ __forceinline__ uint32_t block_scan_1bar(uint32_t v, uint32_t* s_warp,
-                                                    uint32_t* total) {
-    constexpr int NW = BLOCK / 32;
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    uint32_t x = v;
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-        const uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
-        if (lane >= o) x += y;
-    }
-    if (lane == 31) s_warp[warp] = x;
-    __syncthreads();
-    uint32_t t = lane < NW ? s_warp[lane] : 0u;
-#pragma unroll
-    for (int o = 1; o < NW; o <<= 1) {
-        const uint32_t y = __shfl_up_sync(0xffffffffu, t, o);
-        if (lane >= o) t += y;
-    }
-    const uint32_t before = __shfl_sync(0xffffffffu, t, warp > 0 ? warp - 1 : 0);
-    *total = __shfl_sync(0xffffffffu, t, NW - 1);
-    return (warp > 0 ? before : 0u) + x - v;
-}
-
-// Statistics of the kept children for the top-M select: the largest
-// pattern, the count above the candidate range, the candidates inside it.
-struct SelStats {
-    const unsigned long long* range;   // shared: candidate range [lo, hi] (hi == 0: none)
-    unsigned long long out_max;
-    uint32_t above;
-};
-
-// Write one staged item's kept children at pos (and pos + 1) and fold them
-// into the statistics.  Every lane of the warp calls it.
-template <int W>
-__device__ __forceinline__ void stage_emit(const PKey<W>& K, double va, double b, uint32_t o,
-                                           const GateArg<W>& g, PKey<W>* kout, double* cout,
-                                           uint64_t pos, SelStats& st, const CandRegions& cd,
-                                           uint32_t* s_cn) {
-    if (o & 1u) {
-        store_key_stream(kout + pos, K);
-        __stcs(cout + pos, va);
-    }
-    const uint64_t pb = pos + (o & 1u);
-    if (o & 2u) {
-        store_key_stream(kout + pb, key_xor(K, g));
-        __stcs(cout + pb, b);
-    }
-    const unsigned long long a = (o & 1u) ? abs_pattern(va) : 0ULL;
-    const unsigned long long bb = (o & 2u) ? abs_pattern(b) : 0ULL;
-    st.out_max = max(st.out_max, max(a, bb));
-    const unsigned long long hi = st.range[1];
-    if (hi) {   // uniform
-        const unsigned long long lo = st.range[0], w = hi - lo;
-        st.above += (a > hi ? 1u : 0u) + (bb > hi ? 1u : 0u);
-        // a - lo <= w on unsigned values: lo <= a <= hi (a kept child has a > 0)
-        cand_push((o & 1u) && a - lo <= w, a - lo, pos, cd, s_cn);
-        cand_push((o & 2u) && bb - lo <= w, bb - lo, pb, cd, s_cn);
-    }
-}
-
-template <int W>
-struct PassArgs {
-    PKey<W>* keys_s;
-    double* vals_s;     // item i's value at vals_s[shift + i]
-    double* b_s;
-    uint32_t* tab;
-    uint8_t* flags_s;
-    uint32_t* s_warp;
-    uint32_t* s_cn;
-};
-
-// One pass of the gate over n staged strings: phase A (the deferred select's
-// kept set, commutation, sign, the normalised coefficient c and the partner
-// child b = c (-sinh(theta)) s, commuting strings into the pair table),
-// phase B (the partner's b, the merged child, threshold and weight cutoff,
-// the identity's merged coefficient as the next normaliser), a block scan of
-// the kept children, and the write pass from `base` on (room the caller
-// holds).  Three barriers; the staging arrays are free again when it
-// returns.  Returns the kept children written (the same on every thread).
-template <int W, int BLOCK>
-__device__ __forceinline__ uint32_t stage_pass(const PassArgs<W>& a, uint32_t n, uint32_t shift,
-                                               const GateArg<W>& g, const Pending<W>& pd,
-                                               double rnorm, unsigned long long dbits,
-                                               DevCtl* ctl, int nxt, uint32_t tag,
-                                               PKey<W>* kout, double* cout, SelStats& st,
-                                               const CandRegions& cd, unsigned long long base) {
-    double* vals = a.vals_s + shift;
-    // phase A
-    for (uint32_t i = threadIdx.x; i < n; i += BLOCK) {
-        const PKey<W> K = a.keys_s[i];
-        const double raw = vals[i];
-        const bool live = !pd.on || cap_keep(K, raw, pd.T, pd.all_ties, pd.tk);
-        const bool id = key_is_zero(K);
-        if (!live && id) set_status(ctl, ST_TRACE_ZERO, 43);
-        const bool comm = live && commutes(K, g);
-        const bool neg = comm && product_negative(K, g);
-        // the identity's normalised value is exactly 1
-        const double c = id ? 1.0 : __dmul_rn(raw, rnorm);
-        const double m = __longlong_as_double(
-            __double_as_longlong(g.msh) ^ (neg ? (long long)0x8000000000000000ULL : 0LL));
-        vals[i] = c;
-        a.b_s[i] = __dmul_rn(c, m);
-        a.flags_s[i] = (uint8_t)((live ? 1u : 0u) | (comm ? 2u : 0u));
-        if (comm && !pair_insert(K, i, a.tab, tag)) set_status(ctl, ST_CAPACITY, 41);
-    }
-    __syncthreads();                                                  // (1) table built
-    // phase B
-    uint32_t cnt = 0;
-    for (uint32_t i = threadIdx.x; i < n; i += BLOCK) {
-        const uint32_t f = a.flags_s[i];
-        uint32_t o = 0;
-        if (f & 1u) {
-            const PKey<W> K = a.keys_s[i];
-            const double c = vals[i];
-            double pb = 0.0;
-            bool found = false;
-            if (f & 2u) found = pair_find(key_xor(K, g), a.keys_s, a.b_s, a.tab, tag, &pb);
-            const double a1 = __dmul_rn(c, g.ch);                    // cosh(theta) P
-            const double sum = __dadd_rn(a1, pb);                     // + the partner's child
-            const double va = !(f & 2u) ? c : (found ? sum : a1);     // {P,Q} = 0: unchanged
-            const bool emit_b = (f & 2u) && !found;
-            // threshold and weight cutoff on the merged children (Sec. II.B)
-            bool keep_a = above(va, dbits) && light(K, g.maxw);
-            const bool keep_b = emit_b && above(a.b_s[i], dbits) && light(key_xor(K, g), g.maxw);
-            if (key_is_zero(K)) {
-                ctl->norm[nxt] = va;
-                if (!keep_a) set_status(ctl, ST_TRACE_ZERO, 1);
-                keep_a = true;
-            }
-            vals[i] = va;
-            o = (keep_a ? 1u : 0u) | (keep_b ? 2u : 0u);
-        }
-        a.flags_s[i] = (uint8_t)o;
-        cnt += __popc(o);
-    }
-    uint32_t tot;
-    const uint32_t off = block_scan_1bar<BLOCK>(cnt, a.s_warp, &tot);   // (2)
-    // the caller's room starts at base (the same on every thread)
-    uint64_t pos = base + off;
-    // write pass: warp-uniform rounds (the candidate list is filled warp-wide)
-    for (uint32_t i0 = 0; i0 < n; i0 += BLOCK) {
-        const uint32_t i = i0 + threadIdx.x;
-        uint32_t o = 0;
-        PKey<W> K;
-#pragma unroll
-        for (int w = 0; w < W; ++w) { K.x[w] = 0; K.z[w] = 0; }
-        double va = 0.0, b = 0.0;
-        if (i < n) {
-            o = a.flags_s[i];
-            if (o) {
-                K = a.keys_s[i];
-                va = vals[i];
-                b = a.b_s[i];
-            }
-        }
-        stage_emit(K, va, b, o, g, kout, cout, pos, st, cd, a.s_cn);
-        pos += __popc(o);
-    }
-    __syncthreads();                                                  // (3) staging free
-    return tot;
-}
-
-// The tag of the next pass (every thread calls it): slots hold 16-bit tags,
-// so after 65535 passes of one CTA the table is cleared and tags restart.
-template <int W, int BLOCK>
-__device__ __forceinline__ uint32_t next_tag(uint32_t tag, uint32_t* tab) {
-    if (tag < 0xffffu) return tag + 1u;
-    for (uint32_t k = threadIdx.x; k < (uint32_t)StageGeom<W>::kSlots; k += BLOCK) tab[k] = 0u;
-    __syncthreads();
-    return 1u;
-}
-
-template <int W, int BLOCK>
-struct PartOcc {
-    // CTAs per SM the launch bound asks for: the staging and table take
-    // Stage<W>::kBytes of shared memory per CTA
-    static constexpr int kMin = BLOCK <= 256 ? 5 : 2;
-};
 
 // The gate's merge, one partition at a time per CTA.  The partition comes
 // from the scatter buffer (fixed stride, cursor) or is a segment the
@@ -620,20 +166,14 @@ k_gate_part(const PKey<W>* __restrict__ pk, const double* __restrict__ pc,
             uint64_t cap_out, uint64_t chunk, CandRegions cd, ChunkDesc* chunks0,
             ChunkDesc* chunks1, uint32_t max_chunks) {
     using G = Stage<W>;
+    using A = PassArgs<W>;
     constexpr uint32_t C = G::C, S = G::S;
-    extern __shared__ __align__(16) unsigned char smem[];
-    __shared__ uint32_t s_warp[BLOCK / 32];
     __shared__ __align__(8) uint64_t s_bar;
-    __shared__ unsigned long long s_chunk, s_chsz, s_nout, s_range[2];
-    __shared__ uint32_t s_cn, s_long, s_n;
+    __shared__ unsigned long long s_chunk, s_chsz, s_nout;
+    __shared__ uint32_t s_long, s_n;
     __shared__ int s_stop;
     __shared__ Pending<W> s_pd;
     __shared__ double s_rnorm;
-    const PassArgs<W> pa{reinterpret_cast<PKey<W>*>(smem + G::kKeys),
-                         reinterpret_cast<double*>(smem + G::kVals),
-                         reinterpret_cast<double*>(smem + G::kB),
-                         reinterpret_cast<uint32_t*>(smem + G::kTab), smem + G::kFlags, s_warp,
-                         &s_cn};
     const int cur = ctl->cur, nxt = cur ^ 1;
     const bool from_scatter = ctl->part_from_scatter != 0;
     const uint32_t P = ctl->part_P;
@@ -647,9 +187,9 @@ k_gate_part(const PKey<W>* __restrict__ pk, const double* __restrict__ pc,
         s_stop = ctl->status;
         s_pd = pending_of<W>(ctl);
         s_rnorm = ctl->rnorm[cur];
-        s_cn = 0u;
-        s_range[0] = ctl->sp_lo;
-        s_range[1] = ctl->sp_hi;
+        g_cn = 0u;
+        g_range[0] = ctl->sp_lo;
+        g_range[1] = ctl->sp_hi;
         s_nout = 0ULL;      // thread 0 counts the CTA's output and long partitions
         s_long = 0u;
         mbar_init(&s_bar, 1);
@@ -659,14 +199,14 @@ k_gate_part(const PKey<W>* __restrict__ pk, const double* __restrict__ pc,
         ctl->seg = 1;          // the output is the P segments this merge writes
         ctl->seg_P = P;
     }
-    for (uint32_t k = threadIdx.x; k < S; k += BLOCK) pa.tab[k] = 0u;
+    for (uint32_t k = threadIdx.x; k < S; k += BLOCK) A::tab()[k] = 0u;
     __syncthreads();
     if (s_stop) return;
     const Pending<W>& pd = s_pd;
     const double rnorm = s_rnorm;
     PKey<W>* __restrict__ kout = B.key(nxt);
     double* __restrict__ cout = B.coef(nxt);
-    SelStats st{s_range, 0ULL, 0u};
+    SelStats st{0ULL, 0u};
     // this CTA's output chunk: [ch_start, ch_pos) written, [ch_pos, ch_end)
     // free (the same on every thread)
     unsigned long long ch_start = 0, ch_pos = 0, ch_end = 0;
@@ -751,8 +291,8 @@ k_gate_part(const PKey<W>* __restrict__ pk, const double* __restrict__ pc,
                     const uint32_t cb = (uint32_t)(((shift + np) * sizeof(double) + 15) & ~15ULL);
                     fence_async_shared();
                     mbar_expect(&s_bar, kb + cb);
-                    bulk_g2s(pa.keys_s, kp, kb, &s_bar);
-                    bulk_g2s(pa.vals_s, cp - shift, cb, &s_bar);
+                    bulk_g2s(A::keys(), kp, kb, &s_bar);
+                    bulk_g2s(A::vals(), cp - shift, cb, &s_bar);
                 }
                 const bool ok = mbar_wait(&s_bar, parity, kWaitPolls);
                 if (__syncthreads_or(!ok)) {
@@ -767,56 +307,60 @@ k_gate_part(const PKey<W>* __restrict__ pk, const double* __restrict__ pc,
             }
             // every thread has read the cursor: leave it zero for the next scatter
             if (from_scatter && threadIdx.x == 0) cursor[p] = 0u;
-            tag = next_tag<W, BLOCK>(tag, pa.tab);
-            // room: the partition's children (at most 2 np) fit a fresh chunk
-            if (ch_end - ch_pos < 2 * np && !claim(2 * np)) return;
-            const uint32_t tot = stage_pass<W, BLOCK>(pa, (uint32_t)np, shift, g, pd, rnorm, dbits,
-                                                      ctl, nxt, tag, kout, cout, st, cd, ch_pos);
+            tag = next_tag<W, BLOCK>(tag, A::tab());
+            // room for the pass's kept children, claimed once their number
+            // is known: the rest of the current chunk, else a fresh one (the
+            // rest of the old one is left as a hole)
+            unsigned long long at = 0;
+            bool failed = false;
+            const uint32_t tot = stage_pass<W, BLOCK>(
+                (uint32_t)np, shift, g, pd, rnorm, dbits, ctl, nxt, tag, kout, cout, st, cd,
+                [&](uint32_t t) -> unsigned long long {
+                    if (ch_end - ch_pos < t && !claim(t)) {
+                        failed = true;
+                        return ~0ULL;
+                    }
+                    at = ch_pos;
+                    return at;
+                });
+            if (failed) return;
             if (threadIdx.x == 0) {
-                dout[p].off = ch_pos;
+                dout[p].off = at;
                 dout[p].cnt = tot;
                 s_nout += tot;
             }
             ch_pos += tot;
         } else {
-            // a long partition: k sub-passes over the hash classes of the key
-            // with the gate's sites cleared (about C/2 strings each); the
-            // partition's children stay one segment
-            const uint32_t k = (uint32_t)((2 * np + C - 1) / C);
-            if (ch_end - ch_pos < 2 * np && !claim(2 * np)) return;
-            const unsigned long long start = ch_pos;
-            for (uint32_t j = 0; j < k; ++j) {
-                if (threadIdx.x == 0) s_n = 0u;
-                __syncthreads();
-                for (uint64_t i = threadIdx.x; i < np; i += BLOCK) {
-                    const PKey<W> K = load_key_stream(kp + i);
-                    const double raw = __ldcs(cp + i);
-                    const bool live = !pd.on || cap_keep(K, raw, pd.T, pd.all_ties, pd.tk);
-                    if (!live) {
-                        if (key_is_zero(K)) set_status(ctl, ST_TRACE_ZERO, 43);
-                        continue;
-                    }
-                    const uint32_t cls = commutes(K, g) ? sub_pass(K, g, k) : (uint32_t)(i % k);
-                    if (cls != j) continue;
-                    const uint32_t q = atomicAdd(&s_n, 1u);
-                    if (q < C) {
-                        pa.keys_s[q] = K;
-                        pa.vals_s[q] = raw;
-                    } else {
-                        set_status(ctl, ST_CAPACITY, 44);
-                    }
-                }
-                __syncthreads();
-                if (j == 0 && from_scatter && threadIdx.x == 0) cursor[p] = 0u;
-                const uint32_t n = s_n < C ? s_n : C;
-                tag = next_tag<W, BLOCK>(tag, pa.tab);
-                ch_pos += stage_pass<W, BLOCK>(pa, n, 0u, g, pd, rnorm, dbits, ctl, nxt, tag, kout,
-                                               cout, st, cd, ch_pos);
+            // a long partition: sub-passes (merge_long), its children one
+            // segment; written in one round where room for 2 np of them is
+            // at hand or within a fresh chunk, else counted first and given
+            // exactly their number
+            unsigned long long pre = ~0ULL;
+            if (ch_end - ch_pos >= 2 * np) {
+                pre = ch_pos;
+            } else if (2 * np <= chunk) {
+                if (!claim(2 * np)) return;
+                pre = ch_pos;
             }
+            unsigned long long at = pre;
+            bool failed = false;
+            const uint32_t done = merge_long<W, BLOCK>(
+                kp, cp, np, g, pd, rnorm, dbits, ctl, nxt, &tag, kout, cout, st, cd, pre,
+                [&](uint32_t t) -> unsigned long long {
+                    if (ch_end - ch_pos < t && !claim(t)) {
+                        failed = true;
+                        return ~0ULL;
+                    }
+                    at = ch_pos;
+                    return at;
+                },
+                from_scatter ? cursor + p : nullptr, &s_n);
+            if (failed) return;
+            ch_pos += done;
             if (threadIdx.x == 0) {
-                dout[p].off = start;
-                dout[p].cnt = (unsigned int)(ch_pos - start);
-                s_nout += ch_pos - start;
+                dout[p].off = at;
+                dout[p].cnt = done;
+                s_nout += done;
                 s_long += 1u;
             }
         }
@@ -837,7 +381,7 @@ k_gate_part(const PKey<W>* __restrict__ pk, const double* __restrict__ pc,
         record_chunk(ch_start, ch_pos);
         if (s_nout) atomicAdd(&ctl->count[nxt], s_nout);
         if (s_long) atomicAdd(&ctl->stat_long, (unsigned long long)s_long);
-        const uint32_t c = s_cn;
+        const uint32_t c = g_cn;
         cd.cnt[blockIdx.x] = c < cd.region ? c : (uint32_t)cd.region;
         if (c > cd.region) ctl->sp_ovf = 1;
     }
@@ -983,9 +527,12 @@ void plan_windows(int W, std::vector<HostGate>& gates) {
 }
 
 // A merge CTA claims output room in chunks of about an eighth of its share
-// of a bounded state (at most 2^16 terms); what the chunks leave unused is at
-// most one chunk per CTA plus the tails a partition that did not fit left
-// behind, which the state buffers' slack covers.
+// of a bounded state (at most 2^16 terms), or exactly a partition's children
+// when they need more.  What the chunks leave unused is the rest of each
+// CTA's last chunk and, each time a partition did not fit, the rest of the
+// chunk it left (less than that partition's children, at most a chunk): the
+// state buffers' slack covers two chunks per CTA and three quarters of the
+// bound for the second, above the 2 cap_M children a merge writes at most.
 uint64_t merge_chunk(uint64_t cap_M, int max_ctas) {
     uint64_t c = cap_M / (8ULL * (uint64_t)(max_ctas > 0 ? max_ctas : 1));
     uint64_t p = 16;
@@ -994,7 +541,7 @@ uint64_t merge_chunk(uint64_t cap_M, int max_ctas) {
 }
 
 uint64_t merge_slack(uint64_t cap_M, int max_ctas) {
-    return 2ULL * (uint64_t)max_ctas * merge_chunk(cap_M, max_ctas) + cap_M / 4 + 4096;
+    return 2ULL * (uint64_t)max_ctas * merge_chunk(cap_M, max_ctas) + cap_M / 4 * 3 + 4096;
 }
 
 int partition_target_default(int W) {

@@ -577,7 +577,8 @@ __device__ void bitonic_sort_keys(PKey<W>* a, int n_pad) {
 
 template <int W>
 __global__ void __launch_bounds__(1024)
-k_sel_finish(DevCtl* ctl, const PKey<W>* tie_list, uint64_t cap_M, uint64_t cand_hi) {
+k_sel_finish(DevCtl* ctl, const PKey<W>* tie_list, uint64_t cap_M, uint64_t cand_hi,
+             long long* drift, int n_drift, int gate) {
     __shared__ PKey<W> s_ties[SmallTies<W>::kMax];
     __shared__ unsigned int s_cnt;
     if (!ctl->sel_active) return;
@@ -641,10 +642,17 @@ k_sel_finish(DevCtl* ctl, const PKey<W>* tie_list, uint64_t cap_M, uint64_t cand
         ctl->stat_range = ctl->sel_fast ? ctl->sp_hi - ctl->sp_lo
                                         : (ctl->sel_hi > lo ? ctl->sel_hi - lo : 0ULL);
         // the next gate's candidate range: C +- 2^s in pattern units (a
-        // relative width of about 2^(s-52)), centred on this threshold carried
-        // into the next gate's scale (the next gate reads the state rescaled
-        // by 1/c_I, rnorm of the buffer this gate wrote); narrower when the
-        // list ran long or overflowed, wider when the threshold fell outside
+        // relative width of about 2^(s-52)), narrower when the list ran long
+        // or overflowed, wider when the threshold fell outside.  Its centre C:
+        // this threshold moved by what the next gate's threshold moved in the
+        // last layer (the schedule repeats every layer), or, without that,
+        // carried into the next gate's scale (the next gate reads the state
+        // rescaled by 1/c_I, rnorm of the buffer this gate wrote).
+        const unsigned long long Tp = ctl->sp_tprev;
+        const int gi = n_drift > 0 ? gate % n_drift : 0;
+        const int gn = n_drift > 0 ? (gate + 1) % n_drift : 0;
+        if (n_drift > 0) drift[gi] = Tp ? (long long)(T - Tp) : 0LL;
+        ctl->sp_tprev = T;
         int sft = ctl->sp_shift ? ctl->sp_shift : kRangeShift0;
         switch (ctl->sel_fast ? 0 : ctl->sp_reason) {
             case 0: if (ctl->sel_cand_n > cand_hi) sft -= 1; break;
@@ -654,8 +662,14 @@ k_sel_finish(DevCtl* ctl, const PKey<W>* tie_list, uint64_t cap_M, uint64_t cand
         }
         sft = sft < 8 ? 8 : (sft > 60 ? 60 : sft);
         ctl->sp_shift = sft;
-        const double tv = __dmul_rn(__longlong_as_double((long long)T), ctl->rnorm[cur]);
-        const unsigned long long C = abs_pattern(tv);
+        const long long dn = n_drift > 0 ? drift[gn] : 0LL;
+        unsigned long long C;
+        if (dn != 0LL) {
+            const long long c = (long long)T + dn;
+            C = c > 0 ? (unsigned long long)c : 0ULL;
+        } else {
+            C = abs_pattern(__dmul_rn(__longlong_as_double((long long)T), ctl->rnorm[cur]));
+        }
         const unsigned long long h = 1ULL << sft;
         ctl->sp_lo = C > h ? C - h : 0ULL;
         ctl->sp_hi = C + h;
@@ -700,7 +714,7 @@ static SelScratch<W> sel_scratch(const DeviceState& s) {
 }
 
 template <int W>
-static cudaError_t select_w(const DeviceState& s, cudaStream_t st) {
+static cudaError_t select_w(const DeviceState& s, cudaStream_t st, int gate) {
     unsigned long long lo;
     std::memcpy(&lo, &s.delta, sizeof lo);   // delta >= +0: its pattern bounds every kept |c|
     const SelScratch<W> sc = sel_scratch<W>(s);
@@ -716,14 +730,15 @@ static cudaError_t select_w(const DeviceState& s, cudaStream_t st) {
                                                      sc.tie_cap);
     for (int p = 0; p < 8 * W; ++p)
         k_sel_tpass<W><<<s.num_sms, 1024, 0, st>>>(s.ctl, sc.ties, p);
-    k_sel_finish<W><<<1, 1024, 0, st>>>(s.ctl, sc.ties, s.cap_M, s.cand_hi);
+    k_sel_finish<W><<<1, 1024, 0, st>>>(s.ctl, sc.ties, s.cap_M, s.cand_hi, s.sp_drift,
+                                        s.sp_drift ? s.layer_gates : 0, gate);
     return cudaGetLastError();
 }
 
 }  // namespace
 
-cudaError_t launch_select_deferred(const DeviceState& s, cudaStream_t st) {
-    return s.W == 1 ? select_w<1>(s, st) : select_w<2>(s, st);
+cudaError_t launch_select_deferred(const DeviceState& s, cudaStream_t st, int gate) {
+    return s.W == 1 ? select_w<1>(s, st, gate) : select_w<2>(s, st, gate);
 }
 
 int select_deferred_launches(int W) { return 4 + kVPasses + 8 * W + 1; }

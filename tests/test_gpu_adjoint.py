@@ -125,3 +125,41 @@ def test_adjoint_cfg5_size_prefix_matches_oracle(obs_kind):
     assert abs(f_g - f_o) <= 1e-12 * max(1.0, abs(f_o))
     assert H.n_gates == 63
     _close(d_g, d_o)
+
+
+def test_frozen_value_at_alpha_is_the_forward_value():
+    H = wl.adjoint_chain(10)
+    O = wl.energy_observable(H)
+    g = itpp.Propagator(H.n, H.gate_x, H.gate_z, H.alpha, 0.05, 1e-6, 1 << 12, 1)
+    f_adj, _ = g.adjoint(4, O, ckpt_every=2)
+    f_frz = g.frozen_value(4, O, H.alpha, ckpt_every=2)
+    assert abs(f_frz - f_adj) <= 1e-12 * abs(f_adj)
+    o = oracle.Oracle(H.n, H.gate_x, H.gate_z, H.alpha, 0.05, 1e-6, 1 << 12, 1)
+    fa = oracle.FrozenAdjoint(o, 4)
+    a = H.alpha.copy()
+    a[3] += 0.01
+    assert abs(g.frozen_value(4, O, a, ckpt_every=2) - fa.value(O, a)) <= 1e-11 * abs(f_adj)
+
+
+@pytest.mark.parametrize("obs_kind", ["energy", "zz"])
+def test_adjoint_cfg5_full_size_central_differences(obs_kind):
+    """The gradient workload in full (n = 32, 63 parameters, 50 layers,
+    snapshots every 10 layers, |c| <= 1e-7 dropped, at most 2^20 terms):
+    the adjoint gradient of <H> (without its explicit term) and of
+    <Z15 Z16> against central differences (step 1e-5) of the frozen-support
+    forward at six parameters, 1e-7 relative to the largest component."""
+    w = wl.WORKLOADS["adjoint_n32"]
+    H = w.H
+    O = w.observables["energy"] if obs_kind == "energy" else w.observables["Z15Z16"]
+    g = itpp.Propagator.from_workload(w)
+    f, grad = g.adjoint(w.n_layers, O, ckpt_every=10)
+    eps = 1e-5
+    scale = np.max(np.abs(grad))
+    for k in (0, 15, 30, 31, 47, 62):
+        vals = []
+        for sgn in (1, -1):
+            a = H.alpha.copy()
+            a[k] += sgn * eps
+            vals.append(g.frozen_value(w.n_layers, O, a, ckpt_every=10))
+        fd = (vals[0] - vals[1]) / (2 * eps)
+        assert abs(fd - grad[k]) <= 1e-7 * scale, (k, fd, grad[k], scale)

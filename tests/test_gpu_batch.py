@@ -2,7 +2,10 @@
 
 Every instance of a batch must equal its own plain propagation bit for bit
 (string set and coefficient bits), so each is compared with the oracle run
-on that instance's Hamiltonian alone.
+on that instance's Hamiltonian alone.  Both merges of the batch: the
+partitioned one (merge_path 0; with partition_target 2048 every partition
+passes the staging capacity and takes the sub-pass path) and the global
+table (merge_path 2).
 """
 import numpy as np
 import pytest
@@ -31,12 +34,17 @@ def _check_all(bp, ors, hams, what):
         assert_same_state((x[:, :W], z[:, :W], c), (ox, oz, oc), f"{what} instance {b}")
 
 
-def test_batch_mixed_chains_bit_exact():
+PATHS = [(0, 0), (0, 2048), (2, 0)]
+
+
+@pytest.mark.parametrize("merge_path,target", PATHS)
+def test_batch_mixed_chains_bit_exact(merge_path, target):
     hams = [wl.tfim_1d(8, 1.0, 0.7), wl.tfim_1d(12, 1.0, 1.3, periodic=True),
             wl.tfim_1d(5, 0.8, 2.0), wl.tfim_1d(16, 1.0, 0.5), wl.tfim_1d(1, 1.0, 1.0),
             wl.tfim_2d(3, 1.0, 1.5)]
     dtau, delta = 0.05, 1e-5
-    bp = itpp.BatchPropagator(hams, dtau, delta, 1 << 18)
+    bp = itpp.BatchPropagator(hams, dtau, delta, 1 << 18, merge_path=merge_path,
+                              partition_target=target)
     ors = _oracles(hams, dtau, delta, 1 << 18, 0)
     for layer in range(3):
         bp.apply_trotter_layer(1)
@@ -51,11 +59,13 @@ def test_batch_mixed_chains_bit_exact():
     bp.synchronize()
 
 
-def test_batch_two_words_and_random_hamiltonians():
+@pytest.mark.parametrize("merge_path,target", PATHS)
+def test_batch_two_words_and_random_hamiltonians(merge_path, target):
     hams = [wl.random_pauli_hamiltonian(70, 20, 1, max_weight=3),
             wl.random_pauli_hamiltonian(10, 12, 2), wl.tfim_1d(100, 1.0, 1.0, periodic=True)]
     dtau, delta = 0.1, 5e-3
-    bp = itpp.BatchPropagator(hams, dtau, delta, 1 << 17)
+    bp = itpp.BatchPropagator(hams, dtau, delta, 1 << 17, merge_path=merge_path,
+                              partition_target=target)
     ors = _oracles(hams, dtau, delta, 1 << 17, 0)
     bp.apply_trotter_layer(2)
     for o in ors:
@@ -63,12 +73,13 @@ def test_batch_two_words_and_random_hamiltonians():
     _check_all(bp, ors, hams, "W=2")
 
 
+@pytest.mark.parametrize("merge_path", [0, 2])
 @pytest.mark.parametrize("M", [300, 2000])
-def test_batch_top_m_bit_exact(M):
+def test_batch_top_m_bit_exact(M, merge_path):
     hams = [wl.tfim_1d(10, 1.0, 1.0, periodic=True), wl.tfim_1d(14, 1.0, 0.6),
             wl.tfim_1d(6, 1.0, 2.0)]
     dtau, delta = 0.1, 1e-9
-    bp = itpp.BatchPropagator(hams, dtau, delta, M, cap_policy=1)
+    bp = itpp.BatchPropagator(hams, dtau, delta, M, cap_policy=1, merge_path=merge_path)
     ors = _oracles(hams, dtau, delta, M, 1)
     for layer in range(3):
         bp.apply_trotter_layer(1)
@@ -78,9 +89,10 @@ def test_batch_top_m_bit_exact(M):
     assert any(bp.stats(b)["cap_events"] > 0 for b in range(len(hams)))
 
 
-def test_batch_instance_error_is_isolated():
+@pytest.mark.parametrize("merge_path", [0, 2])
+def test_batch_instance_error_is_isolated(merge_path):
     hams = [wl.tfim_1d(12, 1.0, 1.0), wl.tfim_1d(3, 1.0, 1.0)]
-    bp = itpp.BatchPropagator(hams, 0.1, 1e-9, 60, cap_policy=0)
+    bp = itpp.BatchPropagator(hams, 0.1, 1e-9, 60, cap_policy=0, merge_path=merge_path)
     bp.apply_trotter_layer(3)
     counts, statuses = bp.counts()
     assert statuses[0] == 3          # the 12-site chain passes 60 terms
@@ -108,17 +120,24 @@ def test_field_sweep_recipe_sampled_instances():
         assert_same_state(bp.terms(b), o.terms(), f"sweep instance {b} (n={H.n})")
 
 
-def test_autotune_keeps_results_bit_identical():
+@pytest.mark.parametrize("merge_path", [0, 2])
+def test_autotune_keeps_results_bit_identical(merge_path):
     # the tuner resets every instance and installs the fastest shape; any
     # shape gives the plain run's states
     hams = [wl.tfim_1d(10, 1.0, 0.7), wl.tfim_1d(14, 1.0, 1.3, periodic=True),
             wl.tfim_1d(6, 0.8, 2.0), wl.tfim_2d(3, 1.0, 1.5)]
     dtau, delta = 0.05, 1e-6
-    bp = itpp.BatchPropagator(hams, dtau, delta, 1 << 16, 1)
+    bp = itpp.BatchPropagator(hams, dtau, delta, 1 << 16, 1, merge_path=merge_path)
     bp.apply_trotter_layer(2)             # state before tuning is discarded
     r = bp.autotune(probe_layers=2)
-    assert r["main_block"] in (128, 256, 512) and r["main_grid"] in (2, 4, 8)
-    assert r["insert_grid"] in (4, 8, 16) and 25 <= r["table_load_pct"] <= 65
+    assert r["main_block"] in (128, 256, 512)
+    assert r["insert_grid"] in (4, 8, 16)
+    if merge_path == 0:
+        assert 1 <= r["main_grid"] <= 8 and r["table_load_pct"] == 0
+        assert r["partition_target"] in (350, 500, 700, 1000)
+    else:
+        assert r["main_grid"] in (2, 4, 8) and 25 <= r["table_load_pct"] <= 65
+        assert r["partition_target"] == 0
     assert r["candidates"] >= 8 and r["ms_per_probe"] <= r["ms_per_probe_default"]
     counts, _ = bp.counts()
     assert all(int(c) == 1 for c in counts)           # back at the identity

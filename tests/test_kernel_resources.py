@@ -2,7 +2,7 @@
 resource report (`-Xptxas -v`), built exactly as the library is.
 
 The partition merge runs five CTAs of 256 threads per SM, so it has at most
-48 registers; everything else on the main path must keep its keys,
+48 registers; everything else on the main path keeps its keys,
 parameters and partition function out of local memory (an array indexed at
 run time is placed there, and every access then goes through L1).  Runs on
 the CPU: nvcc cross-compiles, nothing is launched.

@@ -183,8 +183,8 @@ def test_noalloc_generation_wrap_clears_the_table(tmp_path):
     hand it call 1's partner coefficients."""
     torch.cuda.set_device(0)
     L = _harness(tmp_path)
-    H = wl.tfim_1d(12, 1.0, 0.8, periodic=True)
-    dtau, delta, k = 0.1, 1e-9, 4
+    H = wl.tfim_1d(10, 1.0, 0.8, periodic=True)
+    dtau, delta, k = 0.1, 1e-6, 4
     ref = itpp.Propagator(H.n, H.gate_x, H.gate_z, H.alpha, dtau, delta, 1 << 18)
     ref.apply_trotter_layer(2)
     x, z, c = ref.terms()
