@@ -216,7 +216,10 @@ k_b_pmerge(BatchBufs<W> S, int step, double delta) {
     __shared__ __align__(8) uint64_t s_bar;
     __shared__ unsigned long long s_base;
     __shared__ uint32_t s_n;
-    __shared__ GateArg<W> s_g;        // the partition's gate, read where used
+    // the partition's gate, read where used (raw storage: a shared variable
+    // gets no constructor, and GateArg has a default member initialiser)
+    __shared__ __align__(16) unsigned char s_g_raw[sizeof(GateArg<W>)];
+    GateArg<W>& s_g = *reinterpret_cast<GateArg<W>*>(s_g_raw);
     __shared__ double s_rnorm;
     if (threadIdx.x == 0) {
         g_cn = 0u;
