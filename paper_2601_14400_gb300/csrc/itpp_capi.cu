@@ -406,7 +406,9 @@ itpp_status itpp_create(int n, const uint64_t* gate_x, const uint64_t* gate_z,
         // partition at the bound (a window group adds up to 4^sites terms)
         s.part_cap = 2 * p->cap_M + p->cap_M / 2 + (1ULL << 18);   // even
         s.part_target = p->partition_target ? p->partition_target : partition_target_default(W);
-        s.part_max = partition_max(p->cap_M, s.part_target);
+        // the scatter aims at half the target at most (after gates whose
+        // stored children outnumber the kept ones)
+        s.part_max = partition_max(p->cap_M, (s.part_target + 1) / 2);
         ok &= cudaMalloc(&s.part_keys, s.part_cap * 16 * W) == cudaSuccess;
         ok &= ok && cudaMalloc(reinterpret_cast<void**>(&s.part_coef), s.part_cap * 8) == cudaSuccess;
         ok &= ok && cudaMalloc(reinterpret_cast<void**>(&s.part_cursor),

@@ -114,7 +114,18 @@ k_part_scatter(Bufs<W> B, DevCtl* ctl, PKey<W>* pk, double* pc, unsigned int* cu
         return;
     }
     const uint64_t n = live_count(ctl, cur);
-    const PartPlan pl = part_plan(n, pbuf_cap, p_max, target);
+    // The merges of a window stage each partition's stored children, which
+    // hold the select's rejected ones until the predicate drops them: when
+    // the previous gate stored g times the terms it kept, aim the kept terms
+    // of a partition at target / g (at least target / 2) so that what the
+    // next merges stage stays near the target instead of passing the staging
+    // capacity.
+    int t_eff = target;
+    if (ctl->pend && n > 0 && ctl->pend_n > n) {
+        const uint64_t t = (uint64_t)target * n / ctl->pend_n;
+        t_eff = t < (uint64_t)(target / 2) ? target / 2 : (int)t;
+    }
+    const PartPlan pl = part_plan(n, pbuf_cap, p_max, t_eff);
     const bool fallback = !f.pair && !window_fits(n_sites, f.sites, n);
     if (fallback) f.pair = 1;
     // the chunks of the previous merge's output
