@@ -103,6 +103,9 @@ def parse():
                          "kernel's DRAM bytes per launch to profiles/traffic.json and exit")
     ap.add_argument("--traffic-command", default="",
                     help="the ncu command that wrote the CSV (recorded beside the bytes)")
+    ap.add_argument("--traffic-scale", type=float, default=1.0,
+                    help="units of the headline launch over units of the captured one "
+                         "(a capture on a smaller bound, scaled by the terms processed)")
     return ap.parse_args()
 
 
@@ -782,7 +785,9 @@ def record_traffic(args):
         return 1
     tot = [d["dram__bytes_read.sum"] + d["dram__bytes_write.sum"] for d in launches]
     rec = {"kernel_class": 1, "kernel": "k_gate_part", "source_digest": source_digest(),
-           "bytes_per_launch": sum(tot) / len(tot), "launches_measured": len(tot),
+           "bytes_per_launch": args.traffic_scale * sum(tot) / len(tot),
+           "measured_bytes_per_launch": sum(tot) / len(tot), "scale": args.traffic_scale,
+           "launches_measured": len(tot),
            "first_launches": [{"dram_read": int(d["dram__bytes_read.sum"]),
                                "dram_write": int(d["dram__bytes_write.sum"]),
                                "duration_ns": int(d.get("gpu__time_duration.sum", 0))}
