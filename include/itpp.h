@@ -143,6 +143,10 @@ typedef struct {
                                * of the library's kernels; 0 while status is ok),
                                * reported together with the status by
                                * itpp_get_stats even when the status is an error */
+    uint64_t merge_retries;   /* partitioned merge with top-M: gates whose merge
+                               * ran twice (it leaves children below the select's
+                               * predicted range unwritten, and runs again in full
+                               * when fewer than cap_M children were kept)        */
 } itpp_stats;
 
 /* ---------------------------------------------------------------------------

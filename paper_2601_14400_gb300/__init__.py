@@ -45,7 +45,8 @@ class itpp_stats(ctypes.Structure):
                 ("table_probes", ctypes.c_uint64), ("kernel_launches", ctypes.c_uint64),
                 ("repartitions", ctypes.c_uint64), ("select_candidates", ctypes.c_uint64),
                 ("select_range", ctypes.c_uint64), ("select_full", ctypes.c_uint64),
-                ("long_partitions", ctypes.c_uint64), ("error_site", ctypes.c_uint64)]
+                ("long_partitions", ctypes.c_uint64), ("error_site", ctypes.c_uint64),
+                ("merge_retries", ctypes.c_uint64)]
 
 
 class ItppError(RuntimeError):

@@ -202,7 +202,8 @@ __global__ void k_import_begin(DevCtl* ctl, uint64_t count) {
         ctl->stat_cands = 0;
         ctl->stat_range = 0;
         ctl->stat_peak = count;
-        ctl->stat_sel_full = ctl->stat_long = 0;
+        ctl->stat_sel_full = ctl->stat_long = ctl->stat_retry = 0;
+        ctl->drop_on = ctl->retry = 0;
         ctl->sel_k = 0;   // reused below as "identity seen" flag
         ctl->pend = 0;
         ctl->seg = 0;
@@ -347,7 +348,8 @@ __global__ void k_reset_identity(BufsA<W> B, DevCtl* ctl) {
         ctl->stat_scatters = 0;
         ctl->stat_cands = 0;
         ctl->stat_range = 0;
-        ctl->stat_sel_full = ctl->stat_long = 0;
+        ctl->stat_sel_full = ctl->stat_long = ctl->stat_retry = 0;
+        ctl->drop_on = ctl->retry = 0;
         ctl->stat_peak = 1;
     }
 }

@@ -151,7 +151,9 @@ itpp_status launch_one_gate(itpp_ctx* h, int k) {
         }
     }
     if (e == cudaSuccess) e = launch_gate_post(h->s, h->stream);
-    h->launches += 3;
+    // scatter, merge, post (partitioned: also the merge's check and its
+    // second launch, which returns at once unless the merge must be redone)
+    h->launches += h->p.merge_path == 0 ? 5 : 3;
     if (e == cudaSuccess && h->s.cap_policy == 1) {
         EventPair* ev2 = prof_begin(h, 2);
         e = launch_cap(h->s, h->stream, k);
@@ -539,6 +541,7 @@ itpp_status itpp_get_stats(itpp_handle h, itpp_stats* o) {
     o->select_range = c.stat_range;
     o->select_full = c.stat_sel_full;
     o->long_partitions = c.stat_long;
+    o->merge_retries = c.stat_retry;
     o->error_site = c.status ? c.err_info : 0;
     o->kernel_launches = h->launches;
     return st;

@@ -126,6 +126,11 @@ struct DevCtl {
     int sel_top;                     // bits of v = pattern - sel_lo still to resolve
     unsigned long long sel_lo;       // offset of the select's values
     unsigned long long stat_sel_full, stat_long;
+    // children below the candidate range left unwritten by this gate's merge
+    // (drop_on); the merge is run again in full when fewer than cap_M were
+    // kept (retry), counted in stat_retry
+    int drop_on, retry;
+    unsigned long long stat_retry;
     // top-M select geometry: largest |c| pattern the gate wrote (partitioned
     // merge), the value the select uses, and the last-CTA counter
     unsigned long long out_max;

@@ -175,7 +175,7 @@ k_gate_part(const PKey<W>* __restrict__ pk, const double* __restrict__ pc,
             unsigned int* __restrict__ cursor, uint64_t pbuf_cap, PartDesc* desc0,
             PartDesc* desc1, Bufs<W> B, DevCtl* ctl, GateArg<W> g, double delta,
             uint64_t cap_out, uint64_t chunk, CandRegions cd, ChunkDesc* chunks0,
-            ChunkDesc* chunks1, uint32_t max_chunks) {
+            ChunkDesc* chunks1, uint32_t max_chunks, int retry_pass) {
     using G = Stage<W>;
     using A = PassArgs<W>;
     constexpr uint32_t C = G::C, S = G::S;
@@ -185,6 +185,7 @@ k_gate_part(const PKey<W>* __restrict__ pk, const double* __restrict__ pc,
     __shared__ int s_stop;
     __shared__ Pending<W> s_pd;
     __shared__ double s_rnorm;
+    __shared__ unsigned long long s_thr;   // kept: pattern above this
     const int cur = ctl->cur, nxt = cur ^ 1;
     const bool from_scatter = ctl->part_from_scatter != 0;
     const uint32_t P = ctl->part_P;
@@ -194,8 +195,9 @@ k_gate_part(const PKey<W>* __restrict__ pk, const double* __restrict__ pc,
     const unsigned long long dbits = (unsigned long long)__double_as_longlong(delta);
     if (threadIdx.x == 0) {
         // one read of the status for the whole CTA (another CTA may set it
-        // meanwhile, and every thread must leave at the same point)
-        s_stop = ctl->status;
+        // meanwhile, and every thread must leave at the same point); the
+        // second launch of a gate runs only when the first one must be redone
+        s_stop = ctl->status || (retry_pass && !ctl->retry);
         s_pd = pending_of<W>(ctl);
         s_rnorm = ctl->rnorm[cur];
         g_cn = 0u;
@@ -205,14 +207,25 @@ k_gate_part(const PKey<W>* __restrict__ pk, const double* __restrict__ pc,
         s_long = 0u;
         mbar_init(&s_bar, 1);
     }
-    if (blockIdx.x == 0 && threadIdx.x == 0 && !ctl->status) {
-        ctl->cand_regions = gridDim.x;
-        ctl->seg = 1;          // the output is the P segments this merge writes
-        ctl->seg_P = P;
+    if (threadIdx.x == 0) {
+        // children below the candidate range are left unwritten: when at
+        // least cap_M children lie at or above it (checked after the merge),
+        // the select would drop every one of them; otherwise the gate's
+        // merge runs again without this (retry_pass)
+        unsigned long long thr = dbits;
+        if (!retry_pass && g_range[1] != 0ULL && g_range[0] > 0ULL && g_range[0] - 1ULL > thr)
+            thr = g_range[0] - 1ULL;
+        s_thr = thr;
+        if (blockIdx.x == 0 && !ctl->status && !retry_pass) ctl->drop_on = thr != dbits;
     }
     for (uint32_t k = threadIdx.x; k < S; k += BLOCK) A::tab()[k] = 0u;
     __syncthreads();
     if (s_stop) return;
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        ctl->cand_regions = gridDim.x;
+        ctl->seg = 1;          // the output is the P segments this merge writes
+        ctl->seg_P = P;
+    }
     const Pending<W>& pd = s_pd;
     const double rnorm = s_rnorm;
     PKey<W>* __restrict__ kout = B.key(nxt);
@@ -316,8 +329,6 @@ k_gate_part(const PKey<W>* __restrict__ pk, const double* __restrict__ pc,
                 }
                 parity ^= 1u;
             }
-            // every thread has read the cursor: leave it zero for the next scatter
-            if (from_scatter && threadIdx.x == 0) cursor[p] = 0u;
             tag = next_tag<W, BLOCK>(tag, A::tab());
             // room for the pass's kept children, claimed once their number
             // is known: the rest of the current chunk, else a fresh one (the
@@ -325,7 +336,7 @@ k_gate_part(const PKey<W>* __restrict__ pk, const double* __restrict__ pc,
             unsigned long long at = 0;
             bool failed = false;
             const uint32_t tot = stage_pass<W, BLOCK>(
-                (uint32_t)np, shift, g, pd, rnorm, dbits, ctl, nxt, tag, kout, cout, st, cd,
+                (uint32_t)np, shift, g, pd, rnorm, s_thr, ctl, nxt, tag, kout, cout, st, cd,
                 [&](uint32_t t) -> unsigned long long {
                     if (ch_end - ch_pos < t && !claim(t)) {
                         failed = true;
@@ -356,7 +367,7 @@ k_gate_part(const PKey<W>* __restrict__ pk, const double* __restrict__ pc,
             unsigned long long at = pre;
             bool failed = false;
             const uint32_t done = merge_long<W, BLOCK>(
-                kp, cp, np, g, pd, rnorm, dbits, ctl, nxt, &tag, kout, cout, st, cd, pre,
+                kp, cp, np, g, pd, rnorm, s_thr, ctl, nxt, &tag, kout, cout, st, cd, pre,
                 [&](uint32_t t) -> unsigned long long {
                     if (ch_end - ch_pos < t && !claim(t)) {
                         failed = true;
@@ -365,7 +376,7 @@ k_gate_part(const PKey<W>* __restrict__ pk, const double* __restrict__ pc,
                     at = ch_pos;
                     return at;
                 },
-                from_scatter ? cursor + p : nullptr, &s_n);
+                nullptr, &s_n);
             if (failed) return;
             ch_pos += done;
             if (threadIdx.x == 0) {
@@ -396,6 +407,29 @@ k_gate_part(const PKey<W>* __restrict__ pk, const double* __restrict__ pc,
         cd.cnt[blockIdx.x] = c < cd.region ? c : (uint32_t)cd.region;
         if (c > cd.region) ctl->sp_ovf = 1;
     }
+}
+
+// After a merge that left the children below the candidate range unwritten:
+// with at least cap_M children kept, the select keeps cap_M of them and every
+// unwritten one lay below them all; with fewer, the unwritten ones are
+// needed, so the merge's output is discarded and the gate's merge runs again
+// in full (its input, the partitions or the previous gate's segments, is
+// still in place).
+__global__ void k_merge_check(DevCtl* ctl, uint64_t cap_M) {
+    if (threadIdx.x != 0 || ctl->status) return;
+    const int nxt = ctl->cur ^ 1;
+    ctl->retry = 0;
+    if (ctl->drop_on && ctl->count[nxt] < cap_M) {
+        ctl->retry = 1;
+        ctl->count[nxt] = 0ULL;
+        ctl->alloc[nxt] = 0ULL;
+        ctl->nchunk[nxt] = 0u;
+        ctl->sp_above = 0ULL;
+        ctl->sp_ovf = 0;
+        ctl->out_max = 0ULL;
+        ctl->stat_retry += 1ULL;
+    }
+    ctl->drop_on = 0;
 }
 
 // ---------------------------------------------------------------------------
@@ -440,10 +474,11 @@ static PartFn<W> part_fn_of(const HostGate& h) {
 
 template <int W>
 static cudaError_t scatter_w(const DeviceState& s, const HostGate& h, int force, cudaStream_t st) {
-    if (force) {
-        cudaError_t e = cudaMemsetAsync(s.part_cursor, 0, (size_t)s.part_max * sizeof(unsigned int), st);
-        if (e != cudaSuccess) return e;
-    }
+    // every gate: the merge leaves the cursors as they are (a gate whose
+    // merge runs again reads its partitions twice), and whether this gate
+    // scatters is decided on the device
+    cudaError_t e = cudaMemsetAsync(s.part_cursor, 0, (size_t)s.part_max * sizeof(unsigned int), st);
+    if (e != cudaSuccess) return e;
     uint64_t gs = (s.buf_cap + 255) / 256;
     const uint64_t lim = (uint64_t)s.num_sms * 8;
     if (gs > lim) gs = lim;
@@ -471,10 +506,13 @@ static cudaError_t merge_wb(const DeviceState& s, const GateArg<W>& g, cudaStrea
     }
     int grid = s.num_sms * per_sm;
     if (grid > s.max_ctas) grid = s.max_ctas;   // one candidate region per CTA
-    k_gate_part<W, BLOCK><<<grid, BLOCK, smem, st>>>(
-        reinterpret_cast<const PKey<W>*>(s.part_keys), s.part_coef, s.part_cursor, s.part_cap,
-        s.part_desc[0], s.part_desc[1], pbufs_of<W>(s), s.ctl, g, s.delta, s.buf_cap, s.chunk,
-        s.cand, s.chunks[0], s.chunks[1], s.max_chunks);
+    for (int pass = 0; pass < 2; ++pass) {
+        k_gate_part<W, BLOCK><<<grid, BLOCK, smem, st>>>(
+            reinterpret_cast<const PKey<W>*>(s.part_keys), s.part_coef, s.part_cursor, s.part_cap,
+            s.part_desc[0], s.part_desc[1], pbufs_of<W>(s), s.ctl, g, s.delta, s.buf_cap,
+            s.chunk, s.cand, s.chunks[0], s.chunks[1], s.max_chunks, pass);
+        if (pass == 0) k_merge_check<<<1, 32, 0, st>>>(s.ctl, s.cap_M);
+    }
     return cudaGetLastError();
 }
 

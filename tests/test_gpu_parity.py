@@ -410,3 +410,34 @@ def test_paper_pair_workload_matches_the_oracle():
         assert abs(E - case["energy"]) <= 1e-12 * abs(case["energy"])
         g.close()
     assert all(c["final_terms"] != 42466 for c in gold["cases"])
+
+
+# ---------------------------------------------------------------------------
+# Children below the select's predicted range, and the merge run again
+# ---------------------------------------------------------------------------
+def test_dropped_children_and_merge_retry_match_oracle():
+    """With top-M the partitioned merge leaves children below the select's
+    predicted range unwritten; when fewer than cap_M children are then kept
+    (the threshold fell below the range: here after every coefficient of the
+    Hamiltonian is cut to a fifth mid-run) the gate's merge runs again in
+    full.  Both cases stay equal to the oracle bit for bit, and the second
+    one occurs."""
+    H = wl.tfim_1d(12, 1.0, 1.0, periodic=True)
+    M, dtau, delta = 3000, 0.1, 1e-9
+    g, o = _pair(H, dtau, delta, cap_M=M, cap_policy=1)
+    for layer in range(4):
+        g.apply_trotter_layer(1)
+        o.apply_layers(1)
+        assert_same_state(g.terms(), o.terms(), f"layer {layer}")
+    assert g.stats()["cap_events"] > 0
+    a2 = np.asarray(H.alpha) * 0.2
+    g.set_alpha(a2)
+    o2 = oracle.Oracle(H.n, H.gate_x, H.gate_z, a2, dtau, delta, M, 1)
+    o2.set_terms(*o.terms())
+    for layer in range(3):
+        g.apply_trotter_layer(1)
+        o2.apply_layers(1)
+        assert_same_state(g.terms(), o2.terms(), f"after the cut, layer {layer}")
+    st = g.stats()
+    print("merge retries", st["merge_retries"], "full selects", st["select_full"])
+    assert st["merge_retries"] > 0
