@@ -8,25 +8,27 @@
 // is scattered once per window into hash partitions of that masked key (one
 // streaming pass, one atomic per term on the partition's cursor), and then
 // every gate of the window runs a persistent kernel that takes one partition
-// at a time per CTA: the partition's terms stay in registers, the commuting
-// ones publish (key, child for the partner) in a shared-memory table, every
-// term merges with its partner's child, and the kept children of the
-// partition are written as one contiguous segment of an output chunk that
-// the CTA claimed beforehand (a global atomic every few hundred partitions,
-// none per partition).  The segments, listed by the partition descriptors,
-// are the partitions of the next gate of the window, so no scatter runs
-// between the gates of a window.  A group holds at most 4^|S| terms; a
-// partition that outgrows the register chunk is merged in sub-passes, each
-// taking the pairs of one hash class of the key with the gate's sites
+// at a time per CTA: the partition is staged in shared memory by bulk (TMA)
+// copies, each commuting string joins its partner {K, QK} in a shared-memory
+// table, one string of each pair computes both merged children, and the kept
+// children of the partition are written as one contiguous segment of an
+// output chunk the CTA holds (room claimed once their number is known, a
+// global atomic every few partitions).  The segments, listed by the partition
+// descriptors, are the partitions of the next gate of the window, so no
+// scatter runs between the gates of a window.  A group holds at most 4^|S|
+// terms; a partition above the staging capacity is merged in sub-passes,
+// each taking the pairs of one hash class of the key with the gate's sites
 // cleared, so no partition size forces a re-partition.  A gate acting on more
 // sites than a window allows is a window of its own, partitioned by its pair
 // key (the member of {K, QK} with the gate's lowest bit clear).
 //
 // The top-M select (Sec. II.C, term bound) is folded into the merge: every
-// kept child is compared with a range around the previous gate's threshold;
-// the merge counts the children above it and lists those inside it, and the
-// select (itpp_select.cu) then works on that short list instead of passing
-// over every coefficient.
+// kept child is compared with a range around the threshold predicted for the
+// gate; the merge counts the children above it, lists those inside it and
+// leaves those below it unwritten (they are dropped by the select whenever at
+// least cap_M children lie at or above the range; otherwise the merge runs
+// again in full), and the select (itpp_select.cu) then works on that short
+// list instead of passing over every coefficient.
 #include "itpp_common.cuh"
 #include "itpp_gate_body.cuh"
 #include "itpp_launch.h"
@@ -169,6 +171,10 @@ k_part_scatter(Bufs<W> B, DevCtl* ctl, PKey<W>* pk, double* pc, unsigned int* cu
 // global atomic.  A partition above the staging capacity is merged in
 // sub-passes: each gathers the strings of one hash class of the key with
 // the gate's sites cleared (which K and Q.K share) into the staging arrays.
+// With a top-M bound the children below the select's predicted range are
+// not written (retry_pass 0); k_merge_check then keeps that output when at
+// least cap_M children were kept, and otherwise the second launch
+// (retry_pass 1) merges the gate again in full from the same input.
 template <int W, int BLOCK>
 __global__ void __launch_bounds__(BLOCK, (PartOcc<W, BLOCK>::kMin))
 k_gate_part(const PKey<W>* __restrict__ pk, const double* __restrict__ pc,
