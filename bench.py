@@ -643,7 +643,14 @@ def run_kscan(args):
                 e0.record(stream)
                 g.apply_trotter_layer(L)
                 e1.record(stream)
-                E = g.expect(Eobs)
+                try:
+                    E = g.expect(Eobs)
+                except itpp.ItppError as err:
+                    st = g.stats(check=False)
+                    row["tried"].append({"K": K, "error": str(err),
+                                         "error_site": st["error_site"]})
+                    g.close()
+                    break
                 ms = e0.elapsed_time(e1)
                 terms = g.count()
                 g.close()
