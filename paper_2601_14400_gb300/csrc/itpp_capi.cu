@@ -339,8 +339,8 @@ itpp_status itpp_create(int n, const uint64_t* gate_x, const uint64_t* gate_z,
         // merge CTAs claim output chunks: room for what the chunks leave
         // unused, and an even count (the L2 bulk prefetch rounds byte ranges
         // to 16 bytes); candidate positions are 32-bit
-        s.chunk = merge_chunk(p->cap_M, s.max_ctas);
-        s.buf_cap += merge_slack(p->cap_M, s.max_ctas);
+        s.chunk = merge_chunk(p->cap_M, s.max_ctas, W);
+        s.buf_cap += merge_slack(p->cap_M, s.max_ctas, W);
         s.buf_cap += s.buf_cap & 1ULL;
         if (s.buf_cap >= (1ULL << 32)) {
             delete h;
@@ -418,9 +418,11 @@ itpp_status itpp_create(int n, const uint64_t* gate_x, const uint64_t* gate_z,
         for (int i = 0; i < 2; ++i)
             ok &= ok && cudaMalloc(reinterpret_cast<void**>(&s.part_desc[i]),
                                    (size_t)s.part_max * sizeof(PartDesc)) == cudaSuccess;
-        // output chunks: every claim takes at least one chunk of the buffer,
-        // and each CTA leaves one partly used
-        s.max_chunks = (uint32_t)(s.buf_cap / s.chunk + 2ULL * (uint64_t)s.max_ctas + 64);
+        // output chunks: every claim takes at least one chunk of the buffer
+        // or (exact claims) one partition's children, and each CTA leaves
+        // one partly used
+        s.max_chunks = (uint32_t)((s.chunk ? s.buf_cap / s.chunk : 0ULL) + s.part_max +
+                                  2ULL * (uint64_t)s.max_ctas + 64);
         for (int i = 0; i < 2; ++i)
             ok &= ok && cudaMalloc(reinterpret_cast<void**>(&s.chunks[i]),
                                    (size_t)s.max_chunks * sizeof(ChunkDesc)) == cudaSuccess;

@@ -103,8 +103,8 @@ uint32_t partition_max(uint64_t cap_M, int target);
 int partition_target_default(int W);
 // Output chunk of the partitioned merge for a term bound, and the room the
 // chunks may leave unused in a state buffer (added to its capacity).
-uint64_t merge_chunk(uint64_t cap_M, int max_ctas);
-uint64_t merge_slack(uint64_t cap_M, int max_ctas);
+uint64_t merge_chunk(uint64_t cap_M, int max_ctas, int W);
+uint64_t merge_slack(uint64_t cap_M, int max_ctas, int W);
 // Group consecutive gates into windows of at most a few sites (sets the
 // window fields of every gate).
 void plan_windows(int W, std::vector<HostGate>& gates);

@@ -585,18 +585,22 @@ void plan_windows(int W, std::vector<HostGate>& gates) {
 // of a bounded state (at most 2^16 terms), or exactly a partition's children
 // when they need more.  What the chunks leave unused is the rest of each
 // CTA's last chunk and, each time a partition did not fit, the rest of the
-// chunk it left (less than that partition's children, at most a chunk): the
-// state buffers' slack covers two chunks per CTA and three quarters of the
-// bound for the second, above the 2 cap_M children a merge writes at most.
-uint64_t merge_chunk(uint64_t cap_M, int max_ctas) {
+// chunk it left (less than that partition's children, at most a quarter of
+// a chunk of at least four times the largest pass's children): the state
+// buffers' slack covers two chunks per CTA and three quarters of the bound
+// for the second, above the 2 cap_M children a merge writes at most.  A
+// bound too small for such chunks (0 returned) makes every claim exact: one
+// claim per partition, nothing left unused.
+uint64_t merge_chunk(uint64_t cap_M, int max_ctas, int W) {
     uint64_t c = cap_M / (8ULL * (uint64_t)(max_ctas > 0 ? max_ctas : 1));
     uint64_t p = 16;
     while (p * 2 <= c && p < (1ULL << 16)) p *= 2;
-    return p;
+    const uint64_t least = 4ULL * 2ULL * (uint64_t)(W == 1 ? Stage<1>::C : Stage<2>::C);
+    return p < least ? 0ULL : p;
 }
 
-uint64_t merge_slack(uint64_t cap_M, int max_ctas) {
-    return 2ULL * (uint64_t)max_ctas * merge_chunk(cap_M, max_ctas) + cap_M / 4 * 3 + 4096;
+uint64_t merge_slack(uint64_t cap_M, int max_ctas, int W) {
+    return 2ULL * (uint64_t)max_ctas * merge_chunk(cap_M, max_ctas, W) + cap_M / 4 * 3 + 4096;
 }
 
 int partition_target_default(int W) {
