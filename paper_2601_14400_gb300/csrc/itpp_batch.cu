@@ -29,6 +29,7 @@ namespace {
 constexpr int kIpt = 2;                               // branch-emit items per thread
 constexpr uint64_t kTileH = 4096;                     // histogram tile
 constexpr uint64_t kTileC = 256;                      // compaction tile
+constexpr unsigned long long kGatherMax = 4096;       // values resolved at once
 
 template <int W>
 struct BatchBufs {
@@ -409,6 +410,7 @@ __global__ void __launch_bounds__(256) k_b_cap_hist(BatchBufs<W> S, int shift) {
     for (unsigned long long t = blockIdx.x; t < total; t += gridDim.x) {
         const int b = owner(S.cap_prefix, S.B, t);
         DevCtl* ctl = S.ctl + b;
+        if (ctl->sel_resolved) continue;   // resolved from its gathered values (uniform)
         for (int k = threadIdx.x; k < kSelBins; k += blockDim.x) h[k] = 0;
         __syncthreads();
         const int cur = ctl->cur;
@@ -431,9 +433,100 @@ __global__ void __launch_bounds__(256) k_b_cap_hist(BatchBufs<W> S, int shift) {
 template <int W>
 __global__ void __launch_bounds__(1024) k_b_cap_pick(BatchBufs<W> S, int shift, int last) {
     DevCtl* ctl = S.ctl + blockIdx.x;
-    if (!ctl->sel_active || ctl->status) return;
+    if (!ctl->sel_active || ctl->status || ctl->sel_resolved) return;
     __shared__ unsigned long long s_part[1024];
-    cap_pick_block(ctl, shift, last, s_part);
+    cap_pick_block(ctl, shift, last, s_part, kGatherMax);
+}
+
+// After a pass whose chosen digit holds at most kGatherMax values: those
+// values (the |c| patterns matching the prefix so far) into a list in the
+// instance's table scratch.
+template <int W>
+__global__ void __launch_bounds__(256) k_b_cap_gather(BatchBufs<W> S) {
+    const unsigned long long total = S.cap_prefix[S.B];
+    for (unsigned long long t = blockIdx.x; t < total; t += gridDim.x) {
+        const int b = owner(S.cap_prefix, S.B, t);
+        DevCtl* ctl = S.ctl + b;
+        if (!ctl->sel_small || ctl->sel_resolved || ctl->status) continue;
+        const int cur = ctl->cur;
+        const uint64_t n = live_count(ctl, cur);
+        const unsigned long long prefix = ctl->sel_prefix, mask = ctl->sel_mask;
+        const double* c = S.c[cur] + (uint64_t)b * S.buf_cap;
+        unsigned long long* list =
+            reinterpret_cast<unsigned long long*>(S.table + (uint64_t)b * S.table_slots);
+        const uint64_t lo = (t - S.cap_prefix[b]) * kTileH;
+        const uint64_t hi = lo + kTileH < n ? lo + kTileH : n;
+        // whole warps iterate together (the append below is warp-wide)
+        for (uint64_t i0 = lo; i0 < hi; i0 += blockDim.x) {
+            const uint64_t i = i0 + threadIdx.x;
+            const unsigned long long v = i < hi ? abs_bits(__ldg(c + i)) : 0ULL;
+            const bool hit = i < hi && (v & mask) == prefix;
+            const unsigned int m = __ballot_sync(0xffffffffu, hit);
+            if (!m) continue;
+            const int lane = threadIdx.x & 31, leader = __ffs(m) - 1;
+            unsigned long long q = 0;
+            if (lane == leader) q = atomicAdd(&ctl->sel_cand_n, (unsigned long long)__popc(m));
+            q = __shfl_sync(0xffffffffu, q, leader);
+            if (hit) {
+                const unsigned long long r = q + __popc(m & ((1u << lane) - 1u));
+                if (r < kGatherMax) list[r] = v;
+                else set_status(ctl, ST_CAPACITY, 49);
+            }
+        }
+    }
+}
+
+// The threshold among the gathered values (one CTA per instance): sorted in
+// shared memory, the sel_k-th largest is the threshold pattern T; the state
+// is then what the last digit pass would leave (prefix T over every bit, the
+// rank within the ties of T, their number).
+template <int W>
+__global__ void __launch_bounds__(1024) k_b_cap_resolve(BatchBufs<W> S) {
+    DevCtl* ctl = S.ctl + blockIdx.x;
+    if (!ctl->sel_active || ctl->status || !ctl->sel_small || ctl->sel_resolved) return;
+    __shared__ unsigned long long v[kGatherMax];
+    __shared__ unsigned int s_gt, s_eq;
+    const unsigned long long n = ctl->sel_cand_n < kGatherMax ? ctl->sel_cand_n : kGatherMax;
+    const unsigned long long* list =
+        reinterpret_cast<const unsigned long long*>(S.table + (uint64_t)blockIdx.x * S.table_slots);
+    for (unsigned int i = threadIdx.x; i < kGatherMax; i += blockDim.x) v[i] = i < n ? list[i] : 0ULL;
+    if (threadIdx.x == 0) s_gt = s_eq = 0u;
+    __syncthreads();
+    // bitonic sort, descending
+    for (unsigned int k = 2; k <= kGatherMax; k <<= 1) {
+        for (unsigned int j = k >> 1; j > 0; j >>= 1) {
+            for (unsigned int i = threadIdx.x; i < kGatherMax; i += blockDim.x) {
+                const unsigned int l = i ^ j;
+                if (l > i) {
+                    const bool desc = (i & k) == 0;
+                    const unsigned long long a = v[i], b = v[l];
+                    if (desc ? (a < b) : (a > b)) {
+                        v[i] = b;
+                        v[l] = a;
+                    }
+                }
+            }
+            __syncthreads();
+        }
+    }
+    const unsigned long long k = ctl->sel_k;   // 1 <= k <= n
+    const unsigned long long T = v[k - 1];
+    unsigned int gt = 0, eq = 0;
+    for (unsigned int i = threadIdx.x; i < n; i += blockDim.x) {
+        gt += v[i] > T ? 1u : 0u;
+        eq += v[i] == T ? 1u : 0u;
+    }
+    atomicAdd(&s_gt, gt);
+    atomicAdd(&s_eq, eq);
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        ctl->sel_prefix = T;
+        ctl->sel_mask = ~0ULL >> 1;
+        ctl->sel_k = k - s_gt;
+        ctl->sel_ties = s_eq;
+        ctl->sel_tie_k = k - s_gt;
+        ctl->sel_resolved = 1;
+    }
 }
 
 template <int W>
@@ -597,6 +690,10 @@ static cudaError_t batch_step_w(const BatchState& s, int step, cudaStream_t st) 
         for (int p = 0; p < 5; ++p) {
             k_b_cap_hist<W><<<grid, 256, 0, st>>>(S, shifts[p]);
             k_b_cap_pick<W><<<s.B, 1024, 0, st>>>(S, shifts[p], p == 4 ? 1 : 0);
+            if (p < 4) {   // instances whose digit held few values: resolved now
+                k_b_cap_gather<W><<<grid, 256, 0, st>>>(S);
+                k_b_cap_resolve<W><<<s.B, 1024, 0, st>>>(S);
+            }
         }
         k_b_cap_ties<W><<<grid, kTileC, 0, st>>>(S);
         const dim3 g2(8, s.B);
@@ -616,7 +713,7 @@ cudaError_t launch_batch_step(const BatchState& s, int step, cudaStream_t st) {
 }
 
 int batch_step_launches(const BatchState& s) {
-    return 4 + (s.cap_policy == 1 ? 5 * 2 + 1 + 8 * s.W * 2 + 3 : 0);
+    return 4 + (s.cap_policy == 1 ? 5 * 2 + 4 * 2 + 1 + 8 * s.W * 2 + 3 : 0);
 }
 
 }  // namespace itpp

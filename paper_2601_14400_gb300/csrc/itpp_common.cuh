@@ -87,6 +87,8 @@ struct DevCtl {
     unsigned long long sel_tie_n;    // tie list length (compacted)
     unsigned long long sel_tie_k;    // rank still to place in the tie select
     int sel_tie_state;               // 0 running, 1 key known, 2 unique prefix found
+    int sel_small, sel_resolved;     // batched select: few values share the prefix
+                                     // (gathered and resolved at once), resolved
     int sel_tie_pass;
     unsigned long long sel_cand_n;   // candidates gathered after the first digit
     // deferred top-M compaction: the state buffer holds pend_n terms of which

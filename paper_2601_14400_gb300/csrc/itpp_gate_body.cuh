@@ -288,6 +288,8 @@ __device__ __forceinline__ int post_one(DevCtl* ctl, uint64_t cap_M, int cap_pol
             ctl->sel_tie_state = 0;
             ctl->sel_tie_pass = 0;
             ctl->sel_cand_n = 0;
+            ctl->sel_small = 0;
+            ctl->sel_resolved = 0;
             for (int w = 0; w < 4; ++w) ctl->sel_tie_key[w] = 0;
             ctl->stat_cap += 1;
         }
@@ -328,8 +330,12 @@ __device__ __forceinline__ unsigned long long scan1024(unsigned long long v,
 }
 
 // Digit holding the k-th largest |c| (one block of 1024 threads).
+// gather_max > 0: when the chosen digit of a pass before the last holds at
+// most gather_max values, mark the select small (the values are gathered and
+// the threshold resolved among them; see the batched select).
 __device__ __forceinline__ void cap_pick_block(DevCtl* ctl, int shift, int last,
-                                               unsigned long long* s_part) {
+                                               unsigned long long* s_part,
+                                               unsigned long long gather_max = 0) {
     constexpr int PER = kSelBins / 1024;
     const int t = threadIdx.x;
     // thread t owns digits kSelBins-1-PER*t ... kSelBins-PER*(t+1) (descending)
@@ -354,6 +360,9 @@ __device__ __forceinline__ void cap_pick_block(DevCtl* ctl, int shift, int last,
                 if (last) {
                     ctl->sel_ties = hv[j];
                     ctl->sel_tie_k = k - run;
+                } else if (gather_max && hv[j] <= gather_max) {
+                    ctl->sel_small = 1;
+                    ctl->sel_cand_n = 0;
                 }
             }
             run += hv[j];
