@@ -81,8 +81,10 @@ typedef struct {
     /* How the children of equal strings are found and summed; every path
      * gives bit-identical states.
      * 0: partitioned merge (default): the state is scattered into hash
-     *    partitions of the pair key {K, Q.K}, and each partition is merged
-     *    through an open-addressing table in shared memory.
+     *    partitions of the key with a window's sites cleared (consecutive
+     *    gates acting on a few sites share one scatter) or of the pair key
+     *    {K, Q.K}, and each partition is merged through an open-addressing
+     *    table in shared memory.
      * 1: sort fallback: the commuting terms' children are radix-sorted on
      *    the whole key (8-bit digits, digits above bit n skipped) and runs of
      *    equal keys are summed by a segmented reduce; anticommuting terms,
@@ -112,8 +114,9 @@ typedef struct {
     int trotter_order;
     /* Partitioned merge (merge_path 0): the mean partition size the scatter
      * aims for, 64..2048 terms (0: the library default).  Larger partitions
-     * amortise the per-partition work, smaller ones keep a window's grown
-     * segments inside one CTA's register chunk. */
+     * amortise the per-partition work; a partition above one CTA's staging
+     * capacity (1,024 terms at W = 1, 512 at W = 2) is merged in slower
+     * sub-passes. */
     int partition_target;
     int reserved[2];
 } itpp_params;
