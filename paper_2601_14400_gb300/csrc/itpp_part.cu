@@ -127,9 +127,20 @@ k_part_scatter(Bufs<W> B, DevCtl* ctl, PKey<W>* pk, double* pc, unsigned int* cu
         const uint64_t t = (uint64_t)target * n / ctl->pend_n;
         t_eff = t < (uint64_t)(target / 2) ? target / 2 : (int)t;
     }
-    const PartPlan pl = part_plan(n, pbuf_cap, p_max, t_eff);
     const bool fallback = !f.pair && !window_fits(n_sites, f.sites, n);
     if (fallback) f.pair = 1;
+    PartPlan pl = part_plan(n, pbuf_cap, p_max, t_eff);
+    if (!f.pair) {
+        // a partition's stride holds a whole group (up to 4^sites strings,
+        // the terms with one pattern outside the window), however the terms
+        // fall
+        const uint64_t gmax = 1ULL << (2 * f.sites);
+        if (pl.R < gmax) {
+            const uint64_t P = pbuf_cap / gmax;
+            pl.P = (uint32_t)(P > 0 ? P : 1);
+            pl.R = pbuf_cap / pl.P;
+        }
+    }
     // the chunks of the previous merge's output
     const bool seg = ctl->seg != 0;
     const uint32_t n_chunks = ctl->nchunk[cur];

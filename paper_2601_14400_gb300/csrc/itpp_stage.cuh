@@ -19,7 +19,7 @@ namespace {
 // terms).
 template <int W> struct PartGeom;
 template <> struct PartGeom<1> {
-    static constexpr int kTarget = 700, kWinSites = 7;
+    static constexpr int kTarget = 700, kWinSites = 5;
 };
 template <> struct PartGeom<2> {
     static constexpr int kTarget = 300, kWinSites = 4;
