@@ -441,3 +441,21 @@ def test_dropped_children_and_merge_retry_match_oracle():
     st = g.stats()
     print("merge retries", st["merge_retries"], "full selects", st["select_full"])
     assert st["merge_retries"] > 0
+
+
+# ---------------------------------------------------------------------------
+# Dense states against the partition layout (no device error)
+# ---------------------------------------------------------------------------
+@pytest.mark.parametrize("n", [16, 20, 24, 28, 32, 48])
+def test_dense_chains_keep_within_partition_strides(n):
+    """Open chains of the field-sweep recipe at a 2^18 bound (top-M), 50
+    layers: the states are dense in the low-weight strings, so the groups of
+    a window (the strings with one pattern outside it) are large; a group
+    must always fit one partition's stride.  The run ends without a device
+    error and the bound holds."""
+    H = wl.tfim_1d(n, 1.0, 1.2)
+    g = itpp.Propagator(H.n, H.gate_x, H.gate_z, H.alpha, 0.02, 1e-7, 1 << 18, 1)
+    g.apply_trotter_layer(50)
+    g.synchronize()
+    st = g.stats()
+    assert st["status"] == 0 and 0 < g.count() <= 1 << 18
