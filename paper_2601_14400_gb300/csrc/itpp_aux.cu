@@ -203,7 +203,7 @@ __global__ void k_import_begin(DevCtl* ctl, uint64_t count) {
         ctl->stat_range = 0;
         ctl->stat_peak = count;
         ctl->stat_sel_full = ctl->stat_long = ctl->stat_retry = 0;
-        ctl->drop_on = ctl->retry = 0;
+        ctl->drop_on = ctl->retry = ctl->scatter_over = 0;
         ctl->sel_k = 0;   // reused below as "identity seen" flag
         ctl->pend = 0;
         ctl->seg = 0;
@@ -349,7 +349,7 @@ __global__ void k_reset_identity(BufsA<W> B, DevCtl* ctl) {
         ctl->stat_cands = 0;
         ctl->stat_range = 0;
         ctl->stat_sel_full = ctl->stat_long = ctl->stat_retry = 0;
-        ctl->drop_on = ctl->retry = 0;
+        ctl->drop_on = ctl->retry = ctl->scatter_over = 0;
         ctl->stat_peak = 1;
     }
 }

@@ -151,9 +151,10 @@ itpp_status launch_one_gate(itpp_ctx* h, int k) {
         }
     }
     if (e == cudaSuccess) e = launch_gate_post(h->s, h->stream);
-    // scatter, merge, post (partitioned: also the merge's check and its
-    // second launch, which returns at once unless the merge must be redone)
-    h->launches += h->p.merge_path == 0 ? 5 : 3;
+    // scatter, merge, post (partitioned: also the scatter's clear and second
+    // launch, the merge's check and second launch, which return at once
+    // unless the scatter or the merge must be redone)
+    h->launches += h->p.merge_path == 0 ? 7 : 3;
     if (e == cudaSuccess && h->s.cap_policy == 1) {
         EventPair* ev2 = prof_begin(h, 2);
         e = launch_cap(h->s, h->stream, k);

@@ -133,6 +133,8 @@ struct DevCtl {
     // kept (retry), counted in stat_retry
     int drop_on, retry;
     unsigned long long stat_retry;
+    int scatter_over;                // a window's partition stride overflowed: the
+                                     // gate scatters again by its pair key
     // top-M select geometry: largest |c| pattern the gate wrote (partitioned
     // merge), the value the select uses, and the last-CTA counter
     unsigned long long out_max;

@@ -88,6 +88,8 @@ __device__ __forceinline__ void scatter_run(const PKey<W>* __restrict__ kin,
                     const uint64_t d = (uint64_t)p * pl.R + pos;
                     store_key(pk + d, K[u]);
                     pc[d] = c[u];
+                } else if (!f.pair) {
+                    ctl->scatter_over = 1;   // the gate scatters again by its pair key
                 } else {
                     set_status(ctl, ST_CAPACITY, 40);
                 }
@@ -100,8 +102,17 @@ template <int W>
 __global__ void __launch_bounds__(256, W == 1 ? 6 : 4)
 k_part_scatter(Bufs<W> B, DevCtl* ctl, PKey<W>* pk, double* pc, unsigned int* cursor,
                uint64_t pbuf_cap, uint32_t p_max, GateArg<W> g, PartFn<W> f, int force,
-               int n_sites, int target, const ChunkDesc* chunks0, const ChunkDesc* chunks1) {
+               int n_sites, int target, const ChunkDesc* chunks0, const ChunkDesc* chunks1,
+               int redo) {
     if (ctl->status) return;
+    // the second launch of a gate's scatter runs only when the first one
+    // found a partition's stride too small for the groups hashed to it; it
+    // scatters by the gate's pair key (pairs always fit) into cleared cursors
+    if (redo) {
+        if (!ctl->scatter_over) return;
+        f.pair = 1;
+        force = 1;
+    }
     const int cur = ctl->cur;
     if (blockIdx.x == 0 && threadIdx.x == 0) {
         // the next merge's counters
@@ -127,15 +138,16 @@ k_part_scatter(Bufs<W> B, DevCtl* ctl, PKey<W>* pk, double* pc, unsigned int* cu
         const uint64_t t = (uint64_t)target * n / ctl->pend_n;
         t_eff = t < (uint64_t)(target / 2) ? target / 2 : (int)t;
     }
-    const bool fallback = !f.pair && !window_fits(n_sites, f.sites, n);
+    const bool fallback = redo || (!f.pair && !window_fits(n_sites, f.sites, n));
     if (fallback) f.pair = 1;
     PartPlan pl = part_plan(n, pbuf_cap, p_max, t_eff);
     if (!f.pair) {
         // a partition's stride holds a whole group (up to 4^sites strings,
         // the terms with one pattern outside the window), however the terms
-        // fall
+        // fall, where that keeps partitions near the target; larger windows
+        // rely on the second scatter by pair key when a stride overflows
         const uint64_t gmax = 1ULL << (2 * f.sites);
-        if (pl.R < gmax) {
+        if (pl.R < gmax && gmax <= 2ULL * (uint64_t)target) {
             const uint64_t P = pbuf_cap / gmax;
             pl.P = (uint32_t)(P > 0 ? P : 1);
             pl.R = pbuf_cap / pl.P;
@@ -169,6 +181,14 @@ k_part_scatter(Bufs<W> B, DevCtl* ctl, PKey<W>* pk, double* pc, unsigned int* cu
     }
 }
 
+
+// Between a gate's two scatter launches: when the first found a stride too
+// small, clear the cursors for the second.
+__global__ void k_scatter_clear(const DevCtl* ctl, unsigned int* cursor, uint32_t p_max) {
+    if (ctl->status || !ctl->scatter_over) return;
+    for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < p_max; i += gridDim.x * blockDim.x)
+        cursor[i] = 0u;
+}
 
 // The gate's merge, one partition at a time per CTA.  The partition comes
 // from the scatter buffer (fixed stride, cursor) or is a segment the
@@ -436,6 +456,7 @@ __global__ void k_merge_check(DevCtl* ctl, uint64_t cap_M) {
     if (threadIdx.x != 0 || ctl->status) return;
     const int nxt = ctl->cur ^ 1;
     ctl->retry = 0;
+    ctl->scatter_over = 0;   // the gate's scatters are done
     if (ctl->drop_on && ctl->count[nxt] < cap_M) {
         ctl->retry = 1;
         ctl->count[nxt] = 0ULL;
@@ -500,11 +521,15 @@ static cudaError_t scatter_w(const DeviceState& s, const HostGate& h, int force,
     const uint64_t lim = (uint64_t)s.num_sms * 8;
     if (gs > lim) gs = lim;
     if (gs < 1) gs = 1;
-    k_part_scatter<W><<<(int)gs, 256, 0, st>>>(pbufs_of<W>(s), s.ctl,
-                                               reinterpret_cast<PKey<W>*>(s.part_keys),
-                                               s.part_coef, s.part_cursor, s.part_cap,
-                                               s.part_max, gate_of<W>(h), part_fn_of<W>(h), force,
-                                               s.n, s.part_target, s.chunks[0], s.chunks[1]);
+    for (int redo = 0; redo < 2; ++redo) {
+        if (redo) k_scatter_clear<<<s.num_sms, 256, 0, st>>>(s.ctl, s.part_cursor, s.part_max);
+        k_part_scatter<W><<<(int)gs, 256, 0, st>>>(pbufs_of<W>(s), s.ctl,
+                                                   reinterpret_cast<PKey<W>*>(s.part_keys),
+                                                   s.part_coef, s.part_cursor, s.part_cap,
+                                                   s.part_max, gate_of<W>(h), part_fn_of<W>(h),
+                                                   force, s.n, s.part_target, s.chunks[0],
+                                                   s.chunks[1], redo);
+    }
     return cudaGetLastError();
 }
 
