@@ -249,25 +249,6 @@ __shared__ unsigned long long g_range[2];   // candidate range [lo, hi] (hi == 0
 // within microseconds; this bound is seconds.
 constexpr uint32_t kWaitPolls = 4096u;
 
-// Slot of a key in a CTA's pair table: a multiply-xor of the key's 32-bit
-// halves and one xorshift-multiply round.  Partitions are chosen by a murmur
-// hash (another function) of another key, so slots spread within one.
-template <int W>
-__device__ __forceinline__ uint32_t slot_hash(const PKey<W>& k) {
-    constexpr uint32_t C[8] = {0x9E3779B1u, 0x85EBCA77u, 0xC2B2AE3Du, 0x27D4EB2Fu,
-                               0x165667B1u, 0xD3A2646Du, 0xFD7046C5u, 0xB55A4F09u};
-    uint32_t h = 0;
-#pragma unroll
-    for (int w = 0; w < W; ++w) {
-        h ^= (uint32_t)k.x[w] * C[4 * w] ^ (uint32_t)(k.x[w] >> 32) * C[4 * w + 1];
-        h ^= (uint32_t)k.z[w] * C[4 * w + 2] ^ (uint32_t)(k.z[w] >> 32) * C[4 * w + 3];
-    }
-    h ^= h >> 15;
-    h *= 0x2C1B3C6Du;
-    h ^= h >> 12;
-    return h;
-}
-
 // Pair table of one pass.  A commuting string K and its partner Q.K agree
 // outside the gate's bits, so both hash the key with those bits cleared and
 // walk the same probe sequence.  A slot holds (tag << 20) | (late << 10) |
@@ -287,25 +268,33 @@ __device__ __forceinline__ uint32_t pair_join(const PKey<W>& K, const GateArg<W>
                                               const PKey<W>* keys_s, uint32_t* tab,
                                               uint32_t tag) {
     constexpr uint32_t S = StageGeom<W>::kSlots;
-    PKey<W> m;
+    constexpr int kBits = S == 2048 ? 11 : 10;
+    static_assert(S == (1u << kBits), "slots");
+    // multiplicative hash of the key with the gate's bits cleared (K and Q.K
+    // agree on it)
+    uint64_t hm = 0;
 #pragma unroll
-    for (int w = 0; w < W; ++w) { m.x[w] = K.x[w] & ~g.qx[w]; m.z[w] = K.z[w] & ~g.qz[w]; }
+    for (int w = 0; w < W; ++w) {
+        hm = (hm ^ (K.x[w] & ~g.qx[w])) * 0x9E3779B97F4A7C15ULL;
+        hm = (hm ^ (K.z[w] & ~g.qz[w])) * 0xC2B2AE3D27D4EB4FULL;
+    }
+    uint32_t h = (uint32_t)(hm >> (64 - kBits));
     const PKey<W> P = key_xor(K, g);
-    uint32_t h = slot_hash(m) & (S - 1);
     for (uint32_t q = 0; q < S; ++q) {
         uint32_t v = tab[h];
         for (;;) {
-            uint32_t want;
-            if ((v >> 20) != tag) {
-                want = (tag << 20) | (i << 10) | i;               // free: claim it
-            } else {
-                const uint32_t e = v & 0x3ffu;
-                if (((v >> 10) & 0x3ffu) != e || !key_eq(keys_s[e], P)) break;   // not mine
-                want = (v & ~(0x3ffu << 10)) | (i << 10);          // my partner, alone
+            if ((v >> 20) != tag) {                                // free: claim it
+                const uint32_t o = atomicCAS(tab + h, v, (tag << 20) | (i << 10) | i);
+                if (o == v) return h;
+                v = o;
+                continue;
             }
-            const uint32_t o = atomicCAS(tab + h, v, want);
-            if (o == v) return h;
-            v = o;
+            const uint32_t e = v & 0x3ffu;
+            if (((v >> 10) & 0x3ffu) != e || !key_eq(keys_s[e], P)) break;   // not mine
+            // my partner, alone: only I write this slot now (a claimed slot is
+            // changed by the partner of its string alone), no atomic needed
+            tab[h] = (v & ~(0x3ffu << 10)) | (i << 10);
+            return h;
         }
         h = (h + 1) & (S - 1);
     }
